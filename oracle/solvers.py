@@ -1,0 +1,300 @@
+"""Iterative solvers for the approximate-deconvolution problem G u = u_bar
+(Section 3, Eq. tau3), written step by step in the paper's order and notation.
+TEST INFRASTRUCTURE ONLY (see the package docstring).
+
+  van_cittert        -- Algorithm 1 (Van Cittert / Richardson, Eq. adm2, Eq. ric)
+  steepest_descent   -- Algorithm 2 (Eq. sd, Eq. sd-a)
+  conjugate_gradient -- Algorithm 3 (Eq. cg1 ... Eq. cg-b)
+  bicgstab           -- Algorithm 4
+
+Readings of points the paper leaves open (each applies to every method):
+  * Inner product (a, b) = integral of a b dx is taken as the plain sum
+    sum_i a_i b_i; the cell volume cancels in every ratio (Eq. inner).
+  * The residual is normalised by the initial residual of the plain start,
+    h_n = ||r_n||_2 / ||u_bar - G u_bar||_2 (Section 4.1: "normalized with
+    respect to the initial residual"); with an explicit starting guess u0 the
+    denominator stays ||u_bar - G u_bar||_2.
+  * The loop "while n < N" is driven by (tol, maxit): h_0 is tested before
+    the loop (h_0 <= tol -> 0 iterations); after every completed pass h_{n+1}
+    is computed from the recurrence residual and the solve stops at the first
+    h <= tol (STATUS_OK) or when maxit passes are done (STATUS_MAXIT).
+    Fixed-N runs are tol = 0, maxit = N. ``iterations`` counts completed
+    passes; N passes of Algorithm 1 give u_N = sum_{n=0}^{N} (I-G)^n u_bar.
+  * BiCGSTAB breakdown (not discussed in the paper): if ||s||/ref <= tol or
+    (t, t) = 0, the pass ends with u += alpha p, r = s and the solve returns
+    STATUS_OK; if rho_{n+1} = 0, (f0, q) = 0 or a scalar is not finite the
+    solve returns STATUS_BREAKDOWN with u from the last full pass.
+  * precision="f32" emulates float32 storage of every vector (rounded after
+    each update and after each application of G) and float32 scalars where
+    they multiply vectors; inner products and scalar recurrences stay in
+    float64. precision="f64" is plain float64 throughout.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .spectral import filter_field
+
+STATUS_OK = 0
+STATUS_MAXIT = 1
+STATUS_BREAKDOWN = 2
+STATUS_NONFINITE = -2
+
+
+@dataclass
+class SolveResult:
+    u: np.ndarray
+    iterations: int
+    status: int
+    history: np.ndarray          # h_0 .. h_iterations
+    true_residual: float         # ||u_bar - G u|| / ref for the returned u
+    trace: dict = field(default_factory=dict)
+
+
+def inner(a, b):
+    """(a, b) = sum_i a_i b_i in float64 (Eq. inner, unweighted)."""
+    return float(np.dot(np.ravel(a).astype(np.float64), np.ravel(b).astype(np.float64)))
+
+
+class _Arith:
+    """Rounding rules of the chosen storage precision."""
+
+    def __init__(self, precision):
+        if precision not in ("f64", "f32"):
+            raise ValueError("precision must be 'f64' or 'f32'")
+        self.f32 = precision == "f32"
+
+    def vec(self, x):
+        x = np.asarray(x, dtype=np.float64)
+        return x.astype(np.float32).astype(np.float64) if self.f32 else x
+
+    def scal(self, a):
+        return float(np.float32(a)) if self.f32 else float(a)
+
+
+def _start(ubar, gamma, u0, ar):
+    ubar = ar.vec(ubar)
+    g_ubar = ar.vec(filter_field(ubar, gamma))
+    ref = math.sqrt(inner(ar.vec(ubar - g_ubar), ar.vec(ubar - g_ubar)))
+    u = ubar.copy() if u0 is None else ar.vec(u0)
+    r = ar.vec(ubar - (g_ubar if u0 is None else ar.vec(filter_field(u, gamma))))
+    return ubar, ref, u, r
+
+
+def _h(rr, ref):
+    return 0.0 if ref == 0.0 else math.sqrt(max(rr, 0.0)) / ref
+
+
+def _finish(ubar, gamma, u, ref, n, status, hist, trace):
+    res = ubar - filter_field(u, gamma)
+    tr = math.sqrt(inner(res, res)) / ref if ref > 0 else math.sqrt(inner(res, res))
+    return SolveResult(u=u, iterations=n, status=status,
+                       history=np.asarray(hist, dtype=np.float64),
+                       true_residual=tr, trace=trace)
+
+
+def _pre_loop(rr0, ref, tol, maxit):
+    """Status decided before the first pass, or None to enter the loop."""
+    h0 = _h(rr0, ref)
+    if not math.isfinite(rr0) or not math.isfinite(ref):
+        return STATUS_NONFINITE, h0
+    if h0 <= tol:
+        return STATUS_OK, h0
+    if maxit <= 0:
+        return STATUS_MAXIT, h0
+    return None, h0
+
+
+def van_cittert(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+    """Algorithm 1: u_{n+1} = u_n + r_n, d_n = G r_n, r_{n+1} = r_n - d_n,
+    starting from u_0 = u_bar, r_0 = u_bar - G u_0 (Eq. adm2, Eq. res, Eq. ric)."""
+    ar = _Arith(precision)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
+    rr = inner(r, r)
+    status, h0 = _pre_loop(rr, ref, tol, maxit)
+    hist = [h0]
+    trace = {"r": [r.copy()]} if record else {}
+    n = 0
+    while status is None:
+        u = ar.vec(u + r)                        # u_{n+1} = u_n + r_n
+        d = ar.vec(filter_field(r, gamma))       # d_n = G r_n
+        r = ar.vec(r - d)                        # r_{n+1} = r_n - d_n
+        n += 1
+        rr = inner(r, r)
+        h = _h(rr, ref)
+        hist.append(h)
+        if record:
+            trace["r"].append(r.copy())
+        if not math.isfinite(rr):
+            status = STATUS_BREAKDOWN
+        elif h <= tol:
+            status = STATUS_OK
+        elif n >= maxit:
+            status = STATUS_MAXIT
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+
+
+def steepest_descent(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+    """Algorithm 2: d_n = G r_n, alpha_n = (r_n, r_n)/(r_n, d_n) (Eq. sd-a),
+    u_{n+1} = u_n + alpha_n r_n (Eq. sd), r_{n+1} = r_n - alpha_n d_n (Eq. rnew1)."""
+    ar = _Arith(precision)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
+    rr = inner(r, r)
+    status, h0 = _pre_loop(rr, ref, tol, maxit)
+    hist = [h0]
+    trace = {"alpha": []} if record else {}
+    n = 0
+    while status is None:
+        d = ar.vec(filter_field(r, gamma))
+        rd = inner(r, d)
+        alpha = rr / rd if rd != 0.0 else float("nan")
+        if not math.isfinite(alpha):
+            status = STATUS_BREAKDOWN
+            break
+        a = ar.scal(alpha)
+        u = ar.vec(u + a * r)
+        r = ar.vec(r - a * d)
+        n += 1
+        rr = inner(r, r)
+        h = _h(rr, ref)
+        hist.append(h)
+        if record:
+            trace["alpha"].append(alpha)
+        if not math.isfinite(rr):
+            status = STATUS_BREAKDOWN
+        elif h <= tol:
+            status = STATUS_OK
+        elif n >= maxit:
+            status = STATUS_MAXIT
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+
+
+def conjugate_gradient(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+    """Algorithm 3: p_0 = r_0, rho_0 = (r_0, r_0); per pass d_n = G p_n,
+    alpha_n = rho_n/(p_n, d_n) (Eq. cg-alpha), u_{n+1} = u_n + alpha_n p_n,
+    r_{n+1} = r_n - alpha_n d_n (Eq. rnew2), rho_{n+1} = (r_{n+1}, r_{n+1}),
+    beta_n = rho_{n+1}/rho_n (Eq. cg-b), p_{n+1} = r_{n+1} + beta_n p_n (Eq. cg4)."""
+    ar = _Arith(precision)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
+    p = r.copy()
+    rho = inner(r, r)
+    status, h0 = _pre_loop(rho, ref, tol, maxit)
+    hist = [h0]
+    trace = {"r": [r.copy()], "p": [p.copy()], "d": [], "alpha": [], "beta": [], "u": [u.copy()]} if record else {}
+    n = 0
+    while status is None:
+        d = ar.vec(filter_field(p, gamma))
+        pd = inner(p, d)
+        alpha = rho / pd if pd != 0.0 else float("nan")
+        if not math.isfinite(alpha):
+            status = STATUS_BREAKDOWN
+            break
+        a = ar.scal(alpha)
+        u = ar.vec(u + a * p)
+        r = ar.vec(r - a * d)
+        rho_new = inner(r, r)
+        beta = rho_new / rho
+        p = ar.vec(r + ar.scal(beta) * p)
+        rho = rho_new
+        n += 1
+        h = _h(rho, ref)
+        hist.append(h)
+        if record:
+            trace["d"].append(d.copy())
+            trace["r"].append(r.copy())
+            trace["p"].append(p.copy())
+            trace["u"].append(u.copy())
+            trace["alpha"].append(alpha)
+            trace["beta"].append(beta)
+        if not math.isfinite(rho):
+            status = STATUS_BREAKDOWN
+        elif h <= tol:
+            status = STATUS_OK
+        elif n >= maxit:
+            status = STATUS_MAXIT
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+
+
+def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+    """Algorithm 4: f_0 = r_0, p_0 = q_0 = 0, alpha_0 = omega_0 = rho_0 = 1; per pass
+    rho_{n+1} = (f_0, r_n), beta_n = (alpha_n/omega_n)(rho_{n+1}/rho_n),
+    p_{n+1} = r_n + beta_n (p_n - omega_n q_n), q_{n+1} = G p_{n+1},
+    alpha_{n+1} = rho_{n+1}/(f_0, q_{n+1}), s_n = r_n - alpha_{n+1} q_{n+1},
+    t_n = G s_n, omega_{n+1} = (s_n, t_n)/(t_n, t_n),
+    u_{n+1} = u_n + alpha_{n+1} p_{n+1} + omega_{n+1} s_n,
+    r_{n+1} = s_n - omega_{n+1} t_n."""
+    ar = _Arith(precision)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
+    f0 = r.copy()
+    p = np.zeros_like(r)
+    q = np.zeros_like(r)
+    alpha = omega = rho = 1.0
+    rr = inner(r, r)
+    status, h0 = _pre_loop(rr, ref, tol, maxit)
+    hist = [h0]
+    trace = {"s": [], "t": [], "r": [r.copy()], "alpha": [], "omega": [], "rho": []} if record else {}
+    n = 0
+    while status is None:
+        rho_new = inner(f0, r)
+        if rho_new == 0.0 or not math.isfinite(rho_new):
+            status = STATUS_BREAKDOWN
+            break
+        beta = (alpha / omega) * (rho_new / rho)
+        if not math.isfinite(beta):
+            status = STATUS_BREAKDOWN
+            break
+        p = ar.vec(r + ar.scal(beta) * ar.vec(p - ar.scal(omega) * q))
+        q = ar.vec(filter_field(p, gamma))
+        fq = inner(f0, q)
+        if fq == 0.0 or not math.isfinite(fq):
+            status = STATUS_BREAKDOWN
+            break
+        alpha = rho_new / fq
+        s = ar.vec(r - ar.scal(alpha) * q)
+        ss = inner(s, s)
+        t = ar.vec(filter_field(s, gamma))
+        tt = inner(t, t)
+        early = _h(ss, ref) <= tol or tt == 0.0
+        omega = 0.0 if early else inner(s, t) / tt
+        if not math.isfinite(omega):
+            status = STATUS_BREAKDOWN
+            break
+        u = ar.vec(ar.vec(u + ar.scal(alpha) * p) + ar.scal(omega) * s)
+        r = ar.vec(s - ar.scal(omega) * t)
+        rho = rho_new
+        n += 1
+        rr = inner(r, r)
+        h = _h(rr, ref)
+        hist.append(h)
+        if record:
+            trace["s"].append(s.copy())
+            trace["t"].append(t.copy())
+            trace["r"].append(r.copy())
+            trace["alpha"].append(alpha)
+            trace["omega"].append(omega)
+            trace["rho"].append(rho_new)
+        if not math.isfinite(rr):
+            status = STATUS_BREAKDOWN
+        elif early or h <= tol:
+            status = STATUS_OK
+        elif n >= maxit:
+            status = STATUS_MAXIT
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+
+
+_METHODS = {
+    "vancittert": van_cittert,
+    "sd": steepest_descent,
+    "cg": conjugate_gradient,
+    "bicgstab": bicgstab,
+}
+
+
+def solve(method, ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+    """Dispatch by method name: 'vancittert', 'sd', 'cg' or 'bicgstab'."""
+    return _METHODS[method](ubar, gamma, tol=tol, maxit=maxit, u0=u0,
+                            precision=precision, record=record)
