@@ -1,0 +1,129 @@
+/*
+ * gad.h -- C ABI of the generalized approximate-deconvolution library.
+ *
+ * The library solves the approximate-deconvolution (AD) problem of San &
+ * Vedula, "Generalized deconvolution procedure for structural modeling of
+ * turbulence": given a filtered field u_bar on a periodic grid, recover u
+ * with G u = u_bar (Section 3, Eq. tau3), where G is the Germano elliptic
+ * differential filter G = (I - delta^2 Laplacian)^{-1}, delta = 1/k_c,
+ * k_c = gamma k_m (Section 4, Eq. df), applied spectrally with transfer
+ * function G_hat(k) = 1/(1 + (|k|/k_c)^2) (Eq. df2). The solve uses Van
+ * Cittert (Algorithm 1), steepest descent (Algorithm 2), conjugate gradient
+ * (Algorithm 3) or BiCGSTAB (Algorithm 4) iterations, all on one GPU.
+ *
+ * Conventions shared by every entry point
+ *   - Fields are real, C-ordered with x contiguous, on a 2*pi-periodic grid:
+ *     field b, point (z, y, x) is element b*P + (z*Ny + y)*Nx + x, with
+ *     P = Nx*Ny*Nz (Nz = 1 in 2D). Wavenumbers are integers; k_m = min(N)/2.
+ *   - Supported sides: every N_d of the form 2^a 3^b, N_d >= 8, with Nx a
+ *     multiple of 4 and Ny, Nz even (powers of two and 2^a 3^b with a >= 2
+ *     cover all workloads).
+ *   - Field pointers are DEVICE pointers owned by the caller, 16-byte
+ *     aligned, holding `batch` contiguous fields of the grid's dtype
+ *     (float for AD_F32, double for AD_F64). The library owns its workspace
+ *     (spectral buffers, Krylov vectors, scalars) inside the context and
+ *     allocates it on the first call for a grid shape and batch size; later
+ *     calls with that shape allocate nothing.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream). Work is enqueued on it.
+ *   - No entry point throws. Arguments are checked before any launch; an
+ *     error returns a negative status and leaves outputs unspecified.
+ *   - A context is not thread safe; use one context per host thread.
+ */
+#ifndef GAD_H
+#define GAD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AD_OK = 0,              /* converged: h_n <= tol                              */
+  AD_MAXIT = 1,           /* maxit passes done without reaching tol (fixed-N)   */
+  AD_BREAKDOWN = 2,       /* a Krylov scalar vanished or is not finite          */
+  AD_ERR_ARG = -1,        /* bad argument (shape, pointer, method, batch ...)   */
+  AD_ERR_NONFINITE = -2,  /* the initial residual is NaN or Inf                 */
+  AD_ERR_CUDA = -3,       /* a CUDA runtime call failed                         */
+  AD_ERR_TIMEOUT = -4,    /* a bounded device wait gave up                      */
+  AD_ERR_NOMEM = -5       /* device allocation of the workspace failed          */
+} ad_status;
+
+typedef enum {
+  AD_VANCITTERT = 0,      /* Algorithm 1 */
+  AD_CG = 1,              /* Algorithm 3 */
+  AD_BICGSTAB = 2,        /* Algorithm 4 */
+  AD_SD = 3               /* Algorithm 2 */
+} ad_method;
+
+typedef enum { AD_F32 = 0, AD_F64 = 1 } ad_dtype;
+
+typedef struct {
+  int ndim;               /* 2 or 3                                              */
+  int64_t n[3];           /* n[0] = Nx (contiguous), n[1] = Ny, n[2] = Nz (3D)   */
+  ad_dtype dtype;         /* storage and FFT precision of the fields            */
+  double gamma;           /* filter strength: k_c = gamma * min(N)/2, 0 < gamma  */
+} ad_grid;
+
+typedef struct ad_ctx ad_ctx;   /* opaque: plans, twiddle tables, workspaces, graphs */
+
+/* Creates a context on CUDA device `device`. *ctx receives the handle, which
+ * the caller releases with ad_destroy. */
+ad_status ad_create(ad_ctx** ctx, int device);
+
+/* Frees every device buffer, graph and stream the context owns. NULL is ignored. */
+void ad_destroy(ad_ctx* ctx);
+
+/* out = G in for `batch` fields (Section 4, Eq. df / Eq. df2, evaluated by
+ * FFT). `in` and `out` may be the same buffer. batch = 0 is a no-op. */
+ad_status ad_filter(ad_ctx* ctx, const ad_grid* grid, const void* in, void* out,
+                    int batch, void* stream);
+
+/* Solves G u = u_bar for `batch` independent fields (Section 3, Eq. tau3) with
+ * `method`, each field with its own scalars and stopping decision.
+ *   ubar        device, batch fields, input (not modified)
+ *   u_out       device, batch fields, output u*; must not alias ubar
+ *   tol, maxit  stop at the first pass n with h_n = ||r_n|| / ||u_bar - G u_bar||
+ *               <= tol (AD_OK) or after maxit passes (AD_MAXIT); tol = 0,
+ *               maxit = N runs exactly N passes. h_0 is tested first
+ *               (h_0 <= tol -> 0 passes). maxit >= 0.
+ *   u0          device initial guess (batch fields) or NULL for u0 = u_bar;
+ *               the history stays normalised by ||u_bar - G u_bar||.
+ *   iterations  host int[batch] (may be NULL): completed passes per field
+ *   status      host ad_status[batch] (may be NULL): outcome per field
+ *   res_hist    host double[batch][maxit+1] (may be NULL): h_0 .. h_iterations
+ *               per field; entries after a field's last pass are unspecified
+ *   true_res    host double[batch] (may be NULL): ||u_bar - G u*|| / ref,
+ *               computed with one extra application of G when requested
+ * Inner products and scalar recurrences run in float64 on the device; AD_F32
+ * fields accumulate products in compensated float32 that is widened to
+ * float64 per thread. The call returns when u_out and the host outputs are
+ * ready. Return value: AD_OK if every field converged, otherwise the status of
+ * the first field that did not (errors before launch are negative). */
+ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void* u_out,
+                        int batch, ad_method method, double tol, int maxit,
+                        const void* u0, int* iterations, ad_status* status,
+                        double* res_hist, double* true_res, void* stream);
+
+/* Enables (1, default) or disables (0) capture of each solve into one CUDA
+ * graph whose iteration loop is a device-side conditional while node. With 0
+ * the host launches the iteration body in chunks and polls the device
+ * between chunks. Returns AD_ERR_ARG for a NULL context. */
+ad_status ad_set_graph_mode(ad_ctx* ctx, int enable);
+
+/* Number of kernel launches the last ad_filter / ad_deconvolve call issued
+ * (graph-internal launches counted per executed kernel node). */
+int64_t ad_last_launch_count(const ad_ctx* ctx);
+
+/* Short English description of a status value (static storage). */
+const char* ad_status_str(ad_status s);
+
+/* Detail of the last error seen by the context (static per-context storage). */
+const char* ad_last_error(const ad_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GAD_H */

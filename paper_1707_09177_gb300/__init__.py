@@ -1,0 +1,203 @@
+"""Python binding of libgad.so, the GB300 approximate-deconvolution library.
+
+Argument marshalling only: every step of filtering and solving runs in the
+library's CUDA kernels. Tensors are torch CUDA tensors (torch provides the
+device memory and the stream); the library sees plain device pointers.
+
+    import paper_1707_09177_gb300 as gad
+    ubar = gad.filter(u, gamma=0.01)                        # G u (Section 4, Eq. df2)
+    res = gad.deconvolve(ubar, gamma=0.01, method="bicgstab", tol=1e-6, maxit=500)
+    res.u, res.iterations, res.status, res.history
+
+Fields are C-ordered with x last: (Ny, Nx) or (Nz, Ny, Nx), with optional
+leading batch dimensions; pass ``ndim`` when the shape is ambiguous (a 3-axis
+tensor may be one 3D field or a batch of 2D fields).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libgad.so")
+
+AD_OK, AD_MAXIT, AD_BREAKDOWN = 0, 1, 2
+AD_ERR_ARG, AD_ERR_NONFINITE, AD_ERR_CUDA, AD_ERR_TIMEOUT, AD_ERR_NOMEM = -1, -2, -3, -4, -5
+METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3}
+AD_F32, AD_F64 = 0, 1
+
+EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_set_graph_mode",
+            "ad_last_launch_count", "ad_status_str", "ad_last_error")
+
+
+class ad_grid(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("n", ctypes.c_int64 * 3), ("dtype", ctypes.c_int),
+                ("gamma", ctypes.c_double)]
+
+
+class GadError(RuntimeError):
+    def __init__(self, status, detail):
+        super().__init__("libgad status %d: %s" % (status, detail))
+        self.status = status
+
+
+_lib = None
+_ctx = {}
+
+
+def library_path():
+    return _LIB_PATH
+
+
+def load(path=None):
+    """Loads libgad.so (building it first if it is missing). Raises if the
+    library cannot be loaded: there is no fallback implementation."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or _LIB_PATH
+    if not os.path.exists(p):
+        from . import build as _b
+        _b.build()
+    lib = ctypes.CDLL(p)
+    c_p, c_i, c_d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    lib.ad_create.argtypes = [ctypes.POINTER(c_p), c_i]
+    lib.ad_create.restype = c_i
+    lib.ad_destroy.argtypes = [c_p]
+    lib.ad_destroy.restype = None
+    lib.ad_filter.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_p]
+    lib.ad_filter.restype = c_i
+    lib.ad_deconvolve.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_i, c_d, c_i, c_p,
+                                  c_p, c_p, c_p, c_p, c_p]
+    lib.ad_deconvolve.restype = c_i
+    lib.ad_set_graph_mode.argtypes = [c_p, c_i]
+    lib.ad_set_graph_mode.restype = c_i
+    lib.ad_last_launch_count.argtypes = [c_p]
+    lib.ad_last_launch_count.restype = ctypes.c_int64
+    lib.ad_status_str.argtypes = [c_i]
+    lib.ad_status_str.restype = ctypes.c_char_p
+    lib.ad_last_error.argtypes = [c_p]
+    lib.ad_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def context(device=None):
+    """The library context for a CUDA device (created on first use)."""
+    import torch
+    lib = load()
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _ctx:
+        h = ctypes.c_void_p()
+        st = lib.ad_create(ctypes.byref(h), dev)
+        if st != AD_OK:
+            raise GadError(st, "ad_create failed on device %d" % dev)
+        _ctx[dev] = h
+    return _ctx[dev]
+
+
+def set_graph_mode(enable, device=None):
+    load().ad_set_graph_mode(context(device), 1 if enable else 0)
+
+
+def last_launch_count(device=None):
+    return int(load().ad_last_launch_count(context(device)))
+
+
+def _check(st, ctx, per_field=False):
+    # AD_ERR_NONFINITE from a solve is a per-field outcome, reported in status[]
+    if st < 0 and not (per_field and st == AD_ERR_NONFINITE):
+        lib = load()
+        raise GadError(st, "%s (%s)" % (lib.ad_status_str(st).decode(), lib.ad_last_error(ctx).decode()))
+
+
+def _grid(t, ndim, gamma):
+    import torch
+    if t.dtype == torch.float32:
+        dt = AD_F32
+    elif t.dtype == torch.float64:
+        dt = AD_F64
+    else:
+        raise TypeError("fields must be float32 or float64, got %s" % t.dtype)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("fields must be contiguous CUDA tensors")
+    if ndim is None:
+        if t.dim() == 2:
+            ndim = 2
+        elif t.dim() == 4:
+            ndim = 3
+        else:
+            raise ValueError("pass ndim=2 or ndim=3 for a %d-axis tensor" % t.dim())
+    if t.dim() < ndim:
+        raise ValueError("tensor has fewer axes than ndim")
+    shape = tuple(t.shape[t.dim() - ndim:])
+    batch = int(np.prod(t.shape[:t.dim() - ndim])) if t.dim() > ndim else 1
+    g = ad_grid()
+    g.ndim = ndim
+    rev = list(reversed(shape)) + [1] * (3 - ndim)
+    for i in range(3):
+        g.n[i] = int(rev[i])
+    g.dtype = dt
+    g.gamma = float(gamma)
+    return g, batch, shape
+
+
+def _stream_ptr(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def filter(u, gamma, ndim=None, out=None, stream=None):
+    """G u for every field of ``u`` (Section 4, Eq. df/df2, evaluated by FFT)."""
+    import torch
+    lib = load()
+    ctx = context(u.device.index)
+    g, batch, _ = _grid(u, ndim, gamma)
+    if out is None:
+        out = torch.empty_like(u)
+    st = lib.ad_filter(ctx, ctypes.byref(g), ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                       batch, _stream_ptr(stream))
+    _check(st, ctx)
+    return out
+
+
+@dataclass
+class Solve:
+    u: object                 # torch tensor, same shape as u_bar
+    iterations: np.ndarray    # int32 [batch]
+    status: np.ndarray        # int32 [batch]
+    history: np.ndarray       # float64 [batch, maxit + 1]; h_0 .. h_iterations valid
+    true_residual: np.ndarray  # float64 [batch] or None
+    launches: int             # kernels the call launched
+
+
+def deconvolve(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, u0=None, ndim=None,
+               out=None, history=True, true_residual=False, stream=None):
+    """Solves G u = u_bar (Section 3, Eq. tau3) for every field of ``ubar``."""
+    import torch
+    lib = load()
+    ctx = context(ubar.device.index)
+    g, batch, _ = _grid(ubar, ndim, gamma)
+    if method not in METHODS:
+        raise ValueError("method must be one of %s" % sorted(METHODS))
+    if out is None:
+        out = torch.empty_like(ubar)
+    if u0 is not None and (u0.shape != ubar.shape or u0.dtype != ubar.dtype or not u0.is_contiguous()):
+        raise ValueError("u0 must match u_bar in shape, dtype and layout")
+    its = np.zeros(batch, dtype=np.int32)
+    sts = np.zeros(batch, dtype=np.int32)
+    hist = np.full((batch, int(maxit) + 1), np.nan) if history else None
+    tr = np.zeros(batch) if true_residual else None
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p()
+    st = lib.ad_deconvolve(ctx, ctypes.byref(g), ctypes.c_void_p(ubar.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                           batch, METHODS[method], float(tol), int(maxit),
+                           ctypes.c_void_p(u0.data_ptr()) if u0 is not None else ctypes.c_void_p(),
+                           ptr(its), ptr(sts), ptr(hist), ptr(tr), _stream_ptr(stream))
+    _check(st, ctx, per_field=True)
+    return Solve(u=out, iterations=its, status=sts, history=hist, true_residual=tr,
+                 launches=int(lib.ad_last_launch_count(ctx)))

@@ -1,0 +1,743 @@
+// C ABI of the approximate-deconvolution library: plans, workspaces, the
+// solver drivers for Algorithms 1-4 and their capture into CUDA graphs.
+//
+// One application of G (Section 4, Eq. df / Eq. df2) is a chain of pass
+// kernels (2D: 3 passes, 3D: 5 passes). A solve is
+//   reset -> [reference pass if u0 given] -> initial residual r0 = u_bar - G u0
+//   -> while (any field active) { one iteration of the chosen algorithm }
+//   -> [CG: deferred u += alpha p] -> [true residual]
+// The iteration body is captured once per (plan, method, tolerance, maxit,
+// buffers) into the body graph of a conditional while node; the scalar
+// recurrences and the loop condition are computed on the device by the last
+// block of each dot-producing pass, so the host waits once per solve.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/gad.h"
+#include "args.h"
+#include "launch.h"
+#include "state.h"
+
+using namespace gad;
+
+namespace {
+
+int phys_h(int i) { return i + (i >> 4); }
+
+bool smooth23(long long n) {
+  if (n < 1) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  return n == 1;
+}
+
+int pow2_part(long long n) {
+  int p = 1;
+  while (n % 2 == 0 && p < (1 << 20)) { n /= 2; p *= 2; }
+  return p;
+}
+
+struct PassCfg {
+  int E = 0, W = 0, T = 0, ld = 0;
+  size_t smem = 0;
+  FftPlan fft{};
+  float rcp_a = 0.f, rcp_b = 0.f;
+  dim3 grid;
+};
+
+struct Plan {
+  int ndim = 2, nx = 0, ny = 0, nz = 1, kxn = 0, batch = 0;
+  bool f64 = false;
+  double gamma = 0.0;
+  long long P = 0, SP = 0;
+  PassCfg xf, xi, fl, yf, yi;
+  const void* twx = nullptr;
+  void *S1 = nullptr, *S2 = nullptr;
+  void *R = nullptr, *Pv = nullptr, *Q = nullptr, *Sv = nullptr, *F0 = nullptr;
+  FieldState* st = nullptr;
+  double* part = nullptr;
+  unsigned* ticket = nullptr;
+  double* hist = nullptr;
+  int hist_cap = 0;
+  std::vector<void*> owned;
+};
+
+struct GraphEntry {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int n_init = 0, n_body = 0, n_fin = 0;
+};
+
+}  // namespace
+
+struct ad_ctx {
+  int device = 0;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  bool use_graph = true;
+  std::map<std::pair<long long, int>, void*> tw;     // (length, is_f64) -> table
+  std::map<std::string, Plan*> plans;
+  std::map<std::string, GraphEntry> graphs;
+  std::string err;
+  int64_t launches = 0;
+};
+
+namespace {
+
+ad_status fail(ad_ctx* c, ad_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+ad_status cuda_fail(ad_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return AD_ERR_CUDA;
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);       \
+  } while (0)
+
+// exp(-2 pi i m / L), m in [0, L), evaluated in long double with exact
+// values at the quarter points.
+template <typename T>
+std::vector<T> twiddle_host(long long L) {
+  std::vector<T> t(2 * L);
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  for (long long m = 0; m < L; ++m) {
+    long double c, s;
+    if (4 * m == L) { c = 0; s = -1; }
+    else if (2 * m == L) { c = -1; s = 0; }
+    else if (4 * m == 3 * L) { c = 0; s = 1; }
+    else {
+      const long double ang = two_pi * (long double)m / (long double)L;
+      c = cosl(ang);
+      s = -sinl(ang);
+    }
+    t[2 * m] = (T)c;
+    t[2 * m + 1] = (T)s;
+  }
+  return t;
+}
+
+ad_status get_table(ad_ctx* ctx, long long L, bool f64, const void** out) {
+  auto key = std::make_pair(L, f64 ? 1 : 0);
+  auto it = ctx->tw.find(key);
+  if (it != ctx->tw.end()) { *out = it->second; return AD_OK; }
+  void* d = nullptr;
+  size_t bytes = (size_t)L * (f64 ? 16 : 8);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return fail(ctx, AD_ERR_NOMEM, "twiddle table"); }
+  cudaError_t e;
+  if (f64) {
+    auto h = twiddle_host<double>(L);
+    e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
+  } else {
+    auto h = twiddle_host<float>(L);
+    e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) { cudaFree(d); return cuda_fail(ctx, e, "twiddle upload"); }
+  ctx->tw[key] = d;
+  *out = d;
+  return AD_OK;
+}
+
+// Balanced radix list for a length L and per-thread element count E.
+bool radices_for(int L, int E, std::vector<int>& rad) {
+  rad.clear();
+  int n = L, a = 0, b = 0;
+  while (n % 2 == 0) { n /= 2; ++a; }
+  while (n % 3 == 0) { n /= 3; ++b; }
+  if (n != 1) return false;
+  if (b > 0 && E % 3 != 0) return false;
+  for (int i = 0; i < b; ++i) rad.push_back(3);
+  const int maxlog = (E % 16 == 0) ? 4 : 3;   // radix 16 for E = 16, 8 for E = 24
+  if (a > 0) {
+    const int ns = (a + maxlog - 1) / maxlog;
+    for (int i = 0; i < ns; ++i) {
+      const int e = a / ns + (i < a % ns ? 1 : 0);
+      rad.push_back(1 << e);
+    }
+  }
+  for (int r : rad) if (E % r != 0) return false;
+  return true;
+}
+
+bool make_fft(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
+  std::vector<int> rad;
+  if (!radices_for(L, E, rad) || rad.size() > 8) return false;
+  fp = FftPlan{};
+  fp.L = L;
+  fp.nst = (int)rad.size();
+  fp.tw = tab;
+  long long ns = 1;
+  for (size_t q = 0; q < rad.size(); ++q) {
+    FftStage& s = fp.st[q];
+    s.radix = rad[q];
+    s.ns = (int)ns;
+    s.tw_step = (int)(Ltab / (ns * rad[q]));
+    s.rcp_lr = 1.0f / (float)(L / rad[q]);
+    s.rcp_ns = 1.0f / (float)ns;
+    ns *= rad[q];
+  }
+  return ns == L;
+}
+
+// Picks the tile width W (a power of two dividing `div`, or any power of two
+// when div = 0) and the block size T = W*L/E closest to 256 threads.
+bool choose_tile(int L, int E, int slots, int div, size_t csize, PassCfg& pc) {
+  int ld = phys_h(slots - 1) + 1;
+  if ((ld & 1) == 0) ++ld;
+  int bestW = 0, bestT = 0;
+  double bestScore = 1e30;
+  for (int W = 1; W <= 4096; W *= 2) {
+    if (div > 0 && div % W != 0) break;
+    const long long tot = (long long)W * L;
+    if (tot % E != 0) continue;
+    const long long T = tot / E;
+    if (T < 1 || T > 512) continue;
+    const size_t smem = (size_t)W * ld * csize;
+    if (smem > 100 * 1024) continue;
+    const double score = std::fabs(std::log2((double)T / 256.0));
+    if (score < bestScore - 1e-9) { bestScore = score; bestW = W; bestT = (int)T; }
+  }
+  if (!bestW) return false;
+  pc.E = E;
+  pc.W = bestW;
+  pc.T = bestT;
+  pc.ld = ld;
+  pc.smem = (size_t)bestW * ld * csize;
+  return true;
+}
+
+int pick_E(int L) { return (L % 3 == 0) ? 24 : 16; }
+
+std::string plan_key(const ad_grid* g, int batch) {
+  char buf[256];
+  snprintf(buf, sizeof buf, "%d:%lld:%lld:%lld:%d:%a:%d", g->ndim, (long long)g->n[0], (long long)g->n[1],
+           g->ndim == 3 ? (long long)g->n[2] : 1LL, (int)g->dtype, g->gamma, batch);
+  return buf;
+}
+
+ad_status check_grid(ad_ctx* ctx, const ad_grid* g) {
+  if (!g) return fail(ctx, AD_ERR_ARG, "grid is NULL");
+  if (g->ndim != 2 && g->ndim != 3) return fail(ctx, AD_ERR_ARG, "ndim must be 2 or 3");
+  if (g->dtype != AD_F32 && g->dtype != AD_F64) return fail(ctx, AD_ERR_ARG, "dtype must be AD_F32 or AD_F64");
+  if (!(g->gamma > 0.0) || !std::isfinite(g->gamma)) return fail(ctx, AD_ERR_ARG, "gamma must be positive");
+  for (int d = 0; d < g->ndim; ++d) {
+    const long long n = g->n[d];
+    if (n < 8 || n > 16384 || !smooth23(n) || (n % 2) != 0)
+      return fail(ctx, AD_ERR_ARG, "each side must be an even 2^a 3^b in [8, 16384]");
+  }
+  if (g->n[0] % 4 != 0) return fail(ctx, AD_ERR_ARG, "Nx must be a multiple of 4");
+  return AD_OK;
+}
+
+ad_status dmalloc(ad_ctx* ctx, Plan* p, void** out, size_t bytes) {
+  if (cudaMalloc(out, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, AD_ERR_NOMEM, "workspace allocation of " + std::to_string(bytes) + " bytes");
+  }
+  p->owned.push_back(*out);
+  return AD_OK;
+}
+
+void free_plan(Plan* p) {
+  for (void* q : p->owned) cudaFree(q);
+  delete p;
+}
+
+ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
+  const std::string key = plan_key(g, batch);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) { *out = it->second; return AD_OK; }
+  Plan* p = new Plan;
+  p->ndim = g->ndim;
+  p->nx = (int)g->n[0];
+  p->ny = (int)g->n[1];
+  p->nz = g->ndim == 3 ? (int)g->n[2] : 1;
+  p->kxn = p->nx / 2 + 1;
+  p->batch = batch;
+  p->f64 = g->dtype == AD_F64;
+  p->gamma = g->gamma;
+  p->P = (long long)p->nx * p->ny * p->nz;
+  p->SP = (long long)p->kxn * p->ny * p->nz;
+  const size_t cs = p->f64 ? 16 : 8, rs = p->f64 ? 8 : 4;
+  ad_status s;
+  const void *tx = nullptr, *ty = nullptr, *tz = nullptr;
+  if ((s = get_table(ctx, p->nx, p->f64, &tx)) != AD_OK) { delete p; return s; }
+  if ((s = get_table(ctx, p->ny, p->f64, &ty)) != AD_OK) { delete p; return s; }
+  if (p->ndim == 3 && (s = get_table(ctx, p->nz, p->f64, &tz)) != AD_OK) { delete p; return s; }
+  p->twx = tx;
+  const int M = p->nx / 2;
+  bool ok = true;
+  // x passes: complex length M (packed real rows), table of length nx, stride 2
+  ok = ok && choose_tile(M, pick_E(M), M + 1, pow2_part(p->ny), cs, p->xf);
+  ok = ok && make_fft(M, p->xf.E, tx, p->nx, p->xf.fft);
+  p->xf.rcp_a = 1.0f / (float)(p->nx / 4);
+  p->xf.rcp_b = 1.0f / (float)(M / 2 + 1);
+  p->xf.grid = dim3(p->ny * p->nz / std::max(p->xf.W, 1), batch);
+  p->xi = p->xf;
+  // filter pass along the last axis
+  const int Lf = p->ndim == 3 ? p->nz : p->ny;
+  const int nseq = p->ndim == 3 ? p->kxn * p->ny : p->kxn;
+  ok = ok && choose_tile(Lf, pick_E(Lf), Lf, 0, cs, p->fl);
+  ok = ok && make_fft(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft);
+  p->fl.rcp_a = 1.0f / (float)(Lf / 2);
+  p->fl.rcp_b = 1.0f / (float)Lf;
+  p->fl.grid = dim3((nseq + std::max(p->fl.W, 1) - 1) / std::max(p->fl.W, 1), batch);
+  if (p->ndim == 3) {
+    ok = ok && choose_tile(p->ny, pick_E(p->ny), p->ny, pow2_part(p->nz), cs, p->yf);
+    ok = ok && make_fft(p->ny, p->yf.E, ty, p->ny, p->yf.fft);
+    p->yf.rcp_a = 1.0f / (float)(p->ny / 2);
+    p->yf.rcp_b = 1.0f / (float)p->ny;
+    p->yf.grid = dim3(p->kxn * (p->nz / std::max(p->yf.W, 1)), batch);
+    p->yi = p->yf;
+  }
+  if (!ok) { delete p; return fail(ctx, AD_ERR_ARG, "no tiling for this grid"); }
+  const size_t vb = (size_t)p->P * batch * rs, sb = (size_t)p->SP * batch * cs;
+  if ((s = dmalloc(ctx, p, &p->S1, sb)) != AD_OK ||
+      (p->ndim == 3 && (s = dmalloc(ctx, p, &p->S2, sb)) != AD_OK)) { free_plan(p); return s; }
+  const unsigned maxblk = std::max(p->xi.grid.x, p->fl.grid.x);
+  if ((s = dmalloc(ctx, p, (void**)&p->st, sizeof(FieldState) * batch)) != AD_OK ||
+      (s = dmalloc(ctx, p, (void**)&p->part, sizeof(double) * 4 * maxblk * batch)) != AD_OK ||
+      (s = dmalloc(ctx, p, (void**)&p->ticket, 64)) != AD_OK) { free_plan(p); return s; }
+  if (cudaMemset(p->ticket, 0, 64) != cudaSuccess) { free_plan(p); return cuda_fail(ctx, cudaGetLastError(), "ticket"); }
+  (void)vb;
+  ctx->plans[key] = p;
+  *out = p;
+  return AD_OK;
+}
+
+ad_status ensure_vectors(ad_ctx* ctx, Plan* p) {
+  if (p->R) return AD_OK;
+  const size_t vb = (size_t)p->P * p->batch * (p->f64 ? 8 : 4);
+  ad_status s;
+  if ((s = dmalloc(ctx, p, &p->R, vb)) != AD_OK || (s = dmalloc(ctx, p, &p->Pv, vb)) != AD_OK ||
+      (s = dmalloc(ctx, p, &p->Q, vb)) != AD_OK || (s = dmalloc(ctx, p, &p->Sv, vb)) != AD_OK ||
+      (s = dmalloc(ctx, p, &p->F0, vb)) != AD_OK)
+    return s;
+  return AD_OK;
+}
+
+void drop_graphs(ad_ctx* ctx) {
+  for (auto& kv : ctx->graphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.g) cudaGraphDestroy(kv.second.g);
+  }
+  ctx->graphs.clear();
+}
+
+ad_status ensure_hist(ad_ctx* ctx, Plan* p, int maxit) {
+  if (maxit + 1 <= p->hist_cap) return AD_OK;
+  drop_graphs(ctx);     // graphs hold the old history pointer
+  if (p->hist) {
+    cudaFree(p->hist);
+    for (auto& q : p->owned) if (q == p->hist) q = nullptr;
+  }
+  p->hist = nullptr;
+  int cap = std::max(maxit + 1, 64);
+  ad_status s = dmalloc(ctx, p, (void**)&p->hist, sizeof(double) * (size_t)cap * p->batch);
+  if (s != AD_OK) return s;
+  p->hist_cap = cap;
+  return AD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Enqueueing one application of G with the given fused prologue/epilogue.
+struct Fwd { int op = XF_COPY; const void* A = nullptr; const void* B = nullptr; void* O1 = nullptr; void* O2 = nullptr; void* O3 = nullptr;
+             bool clear_cond = false; };
+struct Flt { int op = FI_NONE; int stage = SS_NONE; };
+struct Inv { int op = XI_STORE; const void* A = nullptr; const void* B = nullptr; const void* C = nullptr;
+             void* O1 = nullptr; void* O2 = nullptr; int ndots = 0; int stage = SS_NONE; bool set_cond = false; };
+struct Common { FieldState* st = nullptr; SolveConfig cfg{}; cudaGraphConditionalHandle cond = 0; bool in_graph = false; int force = 0; };
+
+template <typename T>
+PassArgs<T> base_args(const Plan* p, const Common& c) {
+  PassArgs<T> a{};
+  a.nx = p->nx; a.ny = p->ny; a.nz = p->nz; a.kxn = p->kxn;
+  a.P = p->P; a.SP = p->SP;
+  a.twx = p->twx;
+  const double kc = p->gamma * (double)std::min(p->nx, std::min(p->ny, p->ndim == 3 ? p->nz : p->ny)) / 2.0;
+  a.kc2 = (T)(kc * kc);
+  a.inv_p = 1.0 / (double)p->P;
+  a.gscale = (T)(1.0 / (double)p->P);
+  a.S1 = p->S1; a.S2 = p->S2;
+  a.st = c.st; a.cfg = c.cfg; a.part = p->part; a.ticket = p->ticket;
+  a.cond = c.cond; a.batch = p->batch; a.force = c.force;
+  return a;
+}
+
+template <typename T>
+void set_pass(PassArgs<T>& a, const PassCfg& pc) {
+  a.W = pc.W; a.ld = pc.ld; a.fft = pc.fft; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b;
+}
+
+template <typename T>
+ad_status enqueue_G(ad_ctx* ctx, Plan* p, cudaStream_t s, const Fwd& fw, const Flt& fl, const Inv& iv,
+                    const Common& c, int* nl) {
+  PassArgs<T> a = base_args<T>(p, c);
+  // forward x pass
+  set_pass(a, p->xf);
+  a.op = fw.op; a.A = (const T*)fw.A; a.B = (const T*)fw.B;
+  a.O1 = (T*)fw.O1; a.O2 = (T*)fw.O2; a.O3 = (T*)fw.O3;
+  a.ndots = 0; a.stage = SS_NONE; a.set_cond = 0; a.clear_cond = (fw.clear_cond && c.in_graph) ? 1 : 0;
+  CK(launch_pass<T>(PK_XFWD, p->xf.E, p->xf.grid, p->xf.T, p->xf.smem, s, a));
+  ++*nl;
+  if (p->ndim == 3) {
+    set_pass(a, p->yf);
+    CK(launch_pass<T>(PK_YFWD, p->yf.E, p->yf.grid, p->yf.T, p->yf.smem, s, a));
+    ++*nl;
+  }
+  a.clear_cond = 0;
+  set_pass(a, p->fl);
+  a.op = fl.op;
+  a.ndots = fl.op == FI_NONE ? 0 : (fl.op == FI_XGX ? 1 : 3);
+  a.stage = fl.stage;
+  CK(launch_pass<T>(PK_FILT, p->fl.E, p->fl.grid, p->fl.T, p->fl.smem, s, a));
+  ++*nl;
+  a.ndots = 0; a.stage = SS_NONE;
+  if (p->ndim == 3) {
+    set_pass(a, p->yi);
+    CK(launch_pass<T>(PK_YINV, p->yi.E, p->yi.grid, p->yi.T, p->yi.smem, s, a));
+    ++*nl;
+  }
+  set_pass(a, p->xi);
+  a.op = iv.op; a.A = (const T*)iv.A; a.B = (const T*)iv.B; a.C = (const T*)iv.C;
+  a.O1 = (T*)iv.O1; a.O2 = (T*)iv.O2; a.O3 = nullptr;
+  a.ndots = iv.ndots; a.stage = iv.stage; a.set_cond = (iv.set_cond && c.in_graph) ? 1 : 0;
+  CK(launch_pass<T>(PK_XINV, p->xi.E, p->xi.grid, p->xi.T, p->xi.smem, s, a));
+  ++*nl;
+  return AD_OK;
+}
+
+struct SolveIO {
+  const void* ubar;
+  void* u;
+  const void* u0;
+  int method;
+  bool want_true;
+};
+
+template <typename T>
+ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  CK(launch_reset_state(p->st, p->batch, s));
+  ++*nl;
+  ad_status r;
+  if (io.u0) {
+    Fwd fw; fw.op = XF_COPY; fw.A = io.ubar;
+    Inv iv; iv.op = XI_RES; iv.A = io.ubar; iv.ndots = 1; iv.stage = SS_REF;
+    if ((r = enqueue_G<T>(ctx, p, s, fw, Flt{}, iv, c, nl)) != AD_OK) return r;
+  }
+  Fwd fw; fw.op = XF_COPY; fw.A = io.u0 ? io.u0 : io.ubar; fw.O1 = io.u;
+  Inv iv; iv.op = XI_INIT; iv.A = io.ubar; iv.O1 = p->R; iv.O2 = io.method == AD_BICGSTAB ? p->F0 : nullptr;
+  iv.ndots = 1; iv.stage = SS_INIT;
+  return enqueue_G<T>(ctx, p, s, fw, Flt{}, iv, c, nl);
+}
+
+template <typename T>
+ad_status enqueue_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  ad_status r;
+  switch (io.method) {
+    case AD_VANCITTERT: {          // Algorithm 1: u += r; d = G r; r -= d
+      Fwd fw; fw.clear_cond = true; fw.op = XF_VC; fw.A = p->R; fw.O1 = io.u;
+      Inv iv; iv.op = XI_VC; iv.O1 = p->R; iv.ndots = 1; iv.stage = SS_VC; iv.set_cond = true;
+      return enqueue_G<T>(ctx, p, s, fw, Flt{}, iv, c, nl);
+    }
+    case AD_SD: {                  // Algorithm 2: d = G r; alpha = (r,r)/(r,d); u += alpha r; r -= alpha d
+      Fwd fw; fw.clear_cond = true; fw.op = XF_COPY; fw.A = p->R;
+      Flt fl; fl.op = FI_XGX; fl.stage = SS_SD_ALPHA;
+      Inv iv; iv.op = XI_SD; iv.O1 = p->R; iv.O2 = io.u; iv.ndots = 1; iv.stage = SS_VC; iv.set_cond = true;
+      return enqueue_G<T>(ctx, p, s, fw, fl, iv, c, nl);
+    }
+    case AD_CG: {                  // Algorithm 3, u += alpha p deferred to the next forward pass
+      Fwd fw; fw.clear_cond = true; fw.op = XF_CG; fw.A = p->R; fw.O1 = io.u; fw.O2 = p->Pv;
+      Flt fl; fl.op = FI_XGX; fl.stage = SS_CG_ALPHA;
+      Inv iv; iv.op = XI_CG; iv.O1 = p->R; iv.ndots = 1; iv.stage = SS_CG_BETA; iv.set_cond = true;
+      return enqueue_G<T>(ctx, p, s, fw, fl, iv, c, nl);
+    }
+    case AD_BICGSTAB: {            // Algorithm 4: two applications of G per pass
+      Fwd f1; f1.clear_cond = true; f1.op = XF_BI_P; f1.A = p->R; f1.B = p->Q; f1.O2 = p->Pv;
+      Inv i1; i1.op = XI_BI_Q; i1.A = p->F0; i1.O1 = p->Q; i1.ndots = 1; i1.stage = SS_BI_ALPHA;
+      if ((r = enqueue_G<T>(ctx, p, s, f1, Flt{}, i1, c, nl)) != AD_OK) return r;
+      Fwd f2; f2.op = XF_BI_S; f2.A = p->R; f2.B = p->Q; f2.O3 = p->Sv;
+      Flt fl; fl.op = FI_SST; fl.stage = SS_BI_OMEGA;
+      Inv i2; i2.op = XI_BI_T; i2.A = p->F0; i2.B = p->Pv; i2.C = p->Sv; i2.O1 = io.u; i2.O2 = p->R;
+      i2.ndots = 2; i2.stage = SS_BI_END; i2.set_cond = true;
+      return enqueue_G<T>(ctx, p, s, f2, fl, i2, c, nl);
+    }
+    default:
+      return fail(ctx, AD_ERR_ARG, "unknown method");
+  }
+}
+
+template <typename T>
+ad_status enqueue_finish(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  if (io.method == AD_CG) {
+    CK(launch_cg_finish<T>((T*)io.u, (const T*)p->Pv, p->st, p->P, p->batch, s));
+    ++*nl;
+  }
+  if (io.want_true) {
+    Common cf = c;
+    cf.force = 1;
+    Fwd fw; fw.op = XF_COPY; fw.A = io.u;
+    Inv iv; iv.op = XI_RES; iv.A = io.ubar; iv.ndots = 1; iv.stage = SS_TRUE;
+    return enqueue_G<T>(ctx, p, s, fw, Flt{}, iv, cf, nl);
+  }
+  return AD_OK;
+}
+
+template <typename T>
+ad_status build_graph(ad_ctx* ctx, Plan* p, const SolveIO& io, Common c, GraphEntry& ge) {
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaGraphConditionalHandleCreate"); }
+  c.cond = h;
+  c.in_graph = true;
+  e = cudaStreamBeginCaptureToGraph(ctx->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
+  int n_init = 0, n_body = 0, n_fin = 0;
+  ad_status st = enqueue_init<T>(ctx, p, ctx->cap, io, c, &n_init);
+  cudaGraph_t body = nullptr;
+  if (st == AD_OK) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, &cg, &deps, nullptr, &nd);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamGetCaptureInfo");
+    cudaGraphNode_t cn = nullptr;
+    cudaGraphNodeParams np{};
+    if (st == AD_OK) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &np);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaGraphAddNode(while)");
+    }
+    if (st == AD_OK) {
+      e = cudaStreamUpdateCaptureDependencies(ctx->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamUpdateCaptureDependencies");
+    }
+    if (st == AD_OK) {
+      body = np.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph(body)");
+      else {
+        st = enqueue_body<T>(ctx, p, ctx->cap2, io, c, &n_body);
+        cudaGraph_t bg = nullptr;
+        e = cudaStreamEndCapture(ctx->cap2, &bg);
+        if (st == AD_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamEndCapture(body)");
+      }
+    }
+    if (st == AD_OK) st = enqueue_finish<T>(ctx, p, ctx->cap, io, c, &n_fin);
+  }
+  cudaGraph_t gout = nullptr;
+  e = cudaStreamEndCapture(ctx->cap, &gout);
+  if (st == AD_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamEndCapture");
+  if (st != AD_OK) { cudaGetLastError(); cudaGraphDestroy(g); return st; }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaGraphInstantiate"); }
+  ge.g = g;
+  ge.exec = exec;
+  ge.n_init = n_init;
+  ge.n_body = n_body;
+  ge.n_fin = n_fin;
+  return AD_OK;
+}
+
+template <typename T>
+ad_status run_solve(ad_ctx* ctx, Plan* p, const SolveIO& io, double tol, int maxit, cudaStream_t stream,
+                    int* loops_out, int* n_body_out) {
+  Common c;
+  c.st = p->st;
+  c.cfg.tol = tol;
+  c.cfg.maxit = maxit;
+  c.cfg.method = io.method;
+  c.cfg.hist = p->hist;
+  c.cfg.hist_ld = p->hist_cap;
+  ad_status st;
+  if (ctx->use_graph) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "|%d|%a|%d|%p|%p|%p|%d", io.method, tol, maxit, io.ubar, io.u, io.u0,
+             io.want_true ? 1 : 0);
+    char pk[128];
+    snprintf(pk, sizeof pk, "%p", (void*)p);
+    const std::string gkey = std::string(pk) + buf;
+    auto it = ctx->graphs.find(gkey);
+    if (it == ctx->graphs.end()) {
+      GraphEntry ge;
+      if ((st = build_graph<T>(ctx, p, io, c, ge)) != AD_OK) return st;
+      it = ctx->graphs.emplace(gkey, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, stream));
+    *loops_out = -1;
+    *n_body_out = it->second.n_body;
+    ctx->launches = it->second.n_init + it->second.n_fin;   // body launches added after readback
+    return AD_OK;
+  }
+  // host-driven loop: body chunks, poll the active flags in between
+  int nl = 0;
+  if ((st = enqueue_init<T>(ctx, p, stream, io, c, &nl)) != AD_OK) return st;
+  std::vector<FieldState> hs(p->batch);
+  int loops = 0;
+  for (;;) {
+    CK(cudaMemcpyAsync(hs.data(), p->st, sizeof(FieldState) * p->batch, cudaMemcpyDeviceToHost, stream));
+    CK(cudaStreamSynchronize(stream));
+    bool any = false;
+    for (auto& f : hs) any = any || f.active;
+    if (!any) break;
+    const int chunk = 4;
+    for (int i = 0; i < chunk; ++i) {
+      int nb = 0;
+      if ((st = enqueue_body<T>(ctx, p, stream, io, c, &nb)) != AD_OK) return st;
+      nl += nb;
+      ++loops;
+    }
+  }
+  if ((st = enqueue_finish<T>(ctx, p, stream, io, c, &nl)) != AD_OK) return st;
+  ctx->launches = nl;
+  *loops_out = loops;
+  return AD_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+extern "C" {
+
+ad_status ad_create(ad_ctx** out, int device) {
+  if (!out) return AD_ERR_ARG;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+    cudaGetLastError();
+    return AD_ERR_ARG;
+  }
+  if (cudaSetDevice(device) != cudaSuccess) return AD_ERR_CUDA;
+  ad_ctx* c = new ad_ctx;
+  c->device = device;
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap2, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return AD_ERR_CUDA;
+  }
+  *out = c;
+  return AD_OK;
+}
+
+void ad_destroy(ad_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  drop_graphs(c);
+  for (auto& kv : c->plans) free_plan(kv.second);
+  for (auto& kv : c->tw) cudaFree(kv.second);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->cap2) cudaStreamDestroy(c->cap2);
+  delete c;
+}
+
+ad_status ad_set_graph_mode(ad_ctx* c, int enable) {
+  if (!c) return AD_ERR_ARG;
+  c->use_graph = enable != 0;
+  return AD_OK;
+}
+
+int64_t ad_last_launch_count(const ad_ctx* c) { return c ? c->launches : 0; }
+
+const char* ad_last_error(const ad_ctx* c) { return c ? c->err.c_str() : "no context"; }
+
+const char* ad_status_str(ad_status s) {
+  switch (s) {
+    case AD_OK: return "converged";
+    case AD_MAXIT: return "maximum number of passes reached";
+    case AD_BREAKDOWN: return "Krylov breakdown (a scalar vanished or is not finite)";
+    case AD_ERR_ARG: return "invalid argument";
+    case AD_ERR_NONFINITE: return "initial residual is not finite";
+    case AD_ERR_CUDA: return "CUDA runtime error";
+    case AD_ERR_TIMEOUT: return "bounded device wait timed out";
+    case AD_ERR_NOMEM: return "device allocation failed";
+  }
+  return "unknown status";
+}
+
+ad_status ad_filter(ad_ctx* ctx, const ad_grid* grid, const void* in, void* out, int batch, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 0) return fail(ctx, AD_ERR_ARG, "batch < 0");
+  if (batch == 0) { ctx->launches = 0; return AD_OK; }
+  if (!in || !out) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
+  if (((uintptr_t)in | (uintptr_t)out) & 15) return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  Common c;
+  Fwd fw; fw.A = in;
+  Inv iv; iv.op = XI_STORE; iv.O1 = out;
+  int nl = 0;
+  s = p->f64 ? enqueue_G<double>(ctx, p, st, fw, Flt{}, iv, c, &nl) : enqueue_G<float>(ctx, p, st, fw, Flt{}, iv, c, &nl);
+  ctx->launches = nl;
+  return s;
+}
+
+ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void* u_out, int batch,
+                        ad_method method, double tol, int maxit, const void* u0, int* iterations,
+                        ad_status* status, double* res_hist, double* true_res, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 0) return fail(ctx, AD_ERR_ARG, "batch < 0");
+  if (method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "unknown method");
+  if (maxit < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return fail(ctx, AD_ERR_ARG, "need maxit >= 0 and finite tol >= 0");
+  if (batch == 0) { ctx->launches = 0; return AD_OK; }
+  if (!ubar || !u_out) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
+  if (ubar == u_out) return fail(ctx, AD_ERR_ARG, "u_out must not alias ubar");
+  if (((uintptr_t)ubar | (uintptr_t)u_out | (uintptr_t)u0) & 15)
+    return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
+  if ((s = ensure_vectors(ctx, p)) != AD_OK) return s;
+  if ((s = ensure_hist(ctx, p, maxit)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  SolveIO io{ubar, u_out, u0, (int)method, true_res != nullptr};
+  int loops = 0, n_body = 0;
+  s = p->f64 ? run_solve<double>(ctx, p, io, tol, maxit, st, &loops, &n_body)
+             : run_solve<float>(ctx, p, io, tol, maxit, st, &loops, &n_body);
+  if (s != AD_OK) return s;
+  std::vector<FieldState> hs(batch);
+  CK(cudaMemcpyAsync(hs.data(), p->st, sizeof(FieldState) * batch, cudaMemcpyDeviceToHost, st));
+  if (res_hist) {
+    CK(cudaMemcpy2DAsync(res_hist, sizeof(double) * (size_t)(maxit + 1), p->hist, sizeof(double) * (size_t)p->hist_cap,
+                         sizeof(double) * (size_t)(maxit + 1), batch, cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  ad_status worst = AD_OK;
+  int maxpass = 0;
+  for (int b = 0; b < batch; ++b) {
+    const FieldState& f = hs[b];
+    if (iterations) iterations[b] = f.iter;
+    if (status) status[b] = (ad_status)f.status;
+    if (true_res) true_res[b] = f.true_res;
+    if (worst == AD_OK && f.status != AD_OK) worst = (ad_status)f.status;
+    maxpass = std::max(maxpass, f.iter + (f.status == AD_BREAKDOWN ? 1 : 0));
+  }
+  if (loops < 0) ctx->launches += (int64_t)std::max(1, maxpass) * n_body;   // graph: body ran max(1, passes) times
+  return worst;
+}
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Launch-argument structures shared by the host driver and the pass kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "state.h"
+
+namespace gad {
+
+// Per-stage description of a mixed-radix Stockham plan.
+struct FftStage {
+  int radix;        // 2, 3, 4, 8 or 16
+  int ns;           // size of the sub-transforms already formed
+  int tw_step;      // twiddle-table stride per unit of r*k
+  float rcp_lr;     // 1 / (L / radix)
+  float rcp_ns;     // 1 / ns
+};
+
+struct FftPlan {
+  int L;            // complex length
+  int nst;          // number of stages
+  FftStage st[8];
+  const void* tw;   // table of exp(-2 pi i m / Ltab), m in [0, Ltab)
+};
+
+// Prologue (forward x pass) opcodes: compute the field to transform and the
+// vector updates that precede G in the algorithm.
+enum XfOp : int {
+  XF_COPY = 0,   // x = A; if O1: O1 = A
+  XF_VC = 1,     // Algorithm 1: U += R (U = O1, R = A); x = R
+  XF_CG = 2,     // Algorithm 3: U += alpha P; P = R + beta P (first pass: P = R); x = P
+  XF_BI_P = 3,   // Algorithm 4: P = R + beta (P - omega Q) (first pass: P = R); x = P
+  XF_BI_S = 4,   // Algorithm 4: S = R - alpha Q; x = S
+};
+
+// Epilogue (inverse x pass) opcodes, y = G x.
+enum XiOp : int {
+  XI_STORE = 0,  // O1 = y
+  XI_INIT = 1,   // r = A - y -> O1 (R), O2 (F0, optional); dot (r, r)
+  XI_RES = 2,    // res = A - y; dot (res, res)
+  XI_VC = 3,     // R -= y; dot (R, R)
+  XI_CG = 4,     // R -= alpha y; dot (R, R)
+  XI_SD = 5,     // U += alpha R; R -= alpha y; dot (R, R)
+  XI_BI_Q = 6,   // Q = y; dot (F0, Q)
+  XI_BI_T = 7,   // t = y; U += alpha P + omega S; R = S - omega t; dots (R, R), (F0, R)
+};
+
+// Filter-pass dot opcodes (Parseval sums over the half spectrum).
+enum FiOp : int {
+  FI_NONE = 0,
+  FI_XGX = 1,    // (x, G x)
+  FI_SST = 2,    // (s, s), (s, G s), (G s, G s)
+};
+
+template <typename T>
+struct PassArgs {
+  int nx, ny, nz, kxn;       // real grid and kxn = nx/2 + 1
+  long long P;               // real points per field
+  long long SP;              // complex points per spectral buffer per field
+  int W, ld;                 // tile width (sequences per block), smem row stride
+  float rcp_a;               // reciprocal helpers for index splits (see kernels)
+  float rcp_b;
+  FftPlan fft;               // transform along this pass's axis
+  const void* twx;           // exp(-2 pi i m / nx) table for the real-FFT split
+  T kc2;                     // k_c^2
+  double inv_p;              // 1/P (Parseval scale of the dots)
+  T gscale;                  // 1/P folded into the filter multiply
+  void* S1;
+  void* S2;
+  const T* A;
+  const T* B;
+  const T* C;
+  T* O1;
+  T* O2;
+  T* O3;
+  int op;
+  int ndots;
+  FieldState* st;            // nullptr for plain filtering
+  SolveConfig cfg;
+  double* part;              // [batch][gridDim.x][4] block partial dots
+  unsigned* ticket;          // arrival counter (reset by the last block)
+  int stage;                 // ScalarStage run by the last block
+  int set_cond;              // last block sets the graph's while-condition
+  cudaGraphConditionalHandle cond;
+  int batch;
+  int force;                 // run for every field regardless of its active flag
+  int clear_cond;            // block (0,0) resets the while-condition to 0 first,
+                             // so the loop ends unless the last pass re-arms it
+};
+
+}  // namespace gad

@@ -1,0 +1,206 @@
+// Shared-memory Stockham FFT building blocks for the filter passes.
+//
+// The filter G of the approximate-deconvolution problem is diagonal in
+// Fourier space (Section 4, Eq. df2), so every application of G is a
+// forward real FFT, a pointwise multiply and an inverse real FFT. These
+// helpers run one axis of such a transform for a tile of W independent
+// sequences held in shared memory.
+//
+// Shared-memory layout of a tile: sequence w occupies a row that starts at
+// w*ld (ld odd, in complex units); element i of the row lives at
+// phys(i) = i + i/16 (one pad slot every 16 elements). The pad makes the
+// power-of-two strides of the Stockham write pattern bank-conflict free, the
+// odd row stride makes column-wise (transposed) access conflict free.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "args.h"
+
+namespace gad {
+
+template <typename T> struct cpx;
+template <> struct cpx<float> { using t = float2; };
+template <> struct cpx<double> { using t = double2; };
+
+__host__ __device__ __forceinline__ int phys(int i) { return i + (i >> 4); }
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+// a * conj(b)
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV, typename C> __device__ __forceinline__ C cmi(C a) {
+  return INV ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+template <typename C, typename S> __device__ __forceinline__ C cscale(C a, S s) { return {a.x * s, a.y * s}; }
+
+// --- small DFTs in registers (forward: exp(-2 pi i nk/R), inverse: +) ---
+template <bool INV, typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = cmi<INV>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft3(C& a0, C& a1, C& a2) {
+  using S = decltype(a0.x);
+  const S h = S(0.86602540378443864676372317075294);  // sqrt(3)/2
+  C t = cadd(a1, a2), d = csub(a1, a2);
+  C m = {a0.x - S(0.5) * t.x, a0.y - S(0.5) * t.y};
+  a0 = cadd(a0, t);
+  C j = cscale(cmi<INV>(d), h);  // (-+ i) sqrt(3)/2 (a1 - a2)
+  a1 = cadd(m, j);
+  a2 = csub(m, j);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft8(C* a) {
+  using S = decltype(a[0].x);
+  const S r = S(0.70710678118654752440084436210485);
+  dft4<INV>(a[0], a[2], a[4], a[6]);
+  dft4<INV>(a[1], a[3], a[5], a[7]);
+  // odd half times W8^k, k = 0..3
+  C o1 = a[3], o2 = a[5], o3 = a[7];
+  o1 = INV ? C{(o1.x - o1.y) * r, (o1.x + o1.y) * r} : C{(o1.x + o1.y) * r, (o1.y - o1.x) * r};
+  o2 = cmi<INV>(o2);
+  o3 = INV ? C{-(o3.x + o3.y) * r, (o3.x - o3.y) * r} : C{(o3.y - o3.x) * r, -(o3.x + o3.y) * r};
+  C e0 = a[0], e1 = a[2], e2 = a[4], e3 = a[6];
+  a[0] = cadd(e0, a[1]);
+  a[4] = csub(e0, a[1]);
+  a[1] = cadd(e1, o1);
+  a[5] = csub(e1, o1);
+  a[2] = cadd(e2, o2);
+  a[6] = csub(e2, o2);
+  a[3] = cadd(e3, o3);
+  a[7] = csub(e3, o3);
+}
+
+template <bool INV, typename C> __device__ __forceinline__ void dft16(C* a) {
+  using S = decltype(a[0].x);
+  // n = 4 n1 + n2, k = k1 + 4 k2: inner 4-point DFTs over n1, twiddle
+  // W16^(n2 k1), outer 4-point DFTs over n2.
+  C b[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C x0 = a[n2], x1 = a[4 + n2], x2 = a[8 + n2], x3 = a[12 + n2];
+    dft4<INV>(x0, x1, x2, x3);
+    b[n2 * 4 + 0] = x0;
+    b[n2 * 4 + 1] = x1;
+    b[n2 * 4 + 2] = x2;
+    b[n2 * 4 + 3] = x3;
+  }
+  const S c1 = S(0.92387953251128675612818318939679);   // cos(pi/8)
+  const S s1 = S(0.38268343236508977172845998403040);   // sin(pi/8)
+  const S r2 = S(0.70710678118654752440084436210485);
+  const S sg = INV ? S(1) : S(-1);
+  // W16^m = cos(m pi/8) + sg i sin(m pi/8)
+  const C w1 = {c1, sg * s1}, w2 = {r2, sg * r2}, w3 = {s1, sg * c1};
+  const C w6 = {-r2, sg * r2}, w9 = {-c1, -sg * s1};
+  b[1 * 4 + 1] = cmul(b[1 * 4 + 1], w1);
+  b[1 * 4 + 2] = cmul(b[1 * 4 + 2], w2);
+  b[1 * 4 + 3] = cmul(b[1 * 4 + 3], w3);
+  b[2 * 4 + 1] = cmul(b[2 * 4 + 1], w2);
+  b[2 * 4 + 2] = cmi<INV>(b[2 * 4 + 2]);   // W16^4
+  b[2 * 4 + 3] = cmul(b[2 * 4 + 3], w6);
+  b[3 * 4 + 1] = cmul(b[3 * 4 + 1], w3);
+  b[3 * 4 + 2] = cmul(b[3 * 4 + 2], w6);
+  b[3 * 4 + 3] = cmul(b[3 * 4 + 3], w9);
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C x0 = b[0 * 4 + k1], x1 = b[1 * 4 + k1], x2 = b[2 * 4 + k1], x3 = b[3 * 4 + k1];
+    dft4<INV>(x0, x1, x2, x3);
+    a[k1 + 0] = x0;
+    a[k1 + 4] = x1;
+    a[k1 + 8] = x2;
+    a[k1 + 12] = x3;
+  }
+}
+
+template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* v) {
+  if constexpr (R == 2) dft2<INV>(v[0], v[1]);
+  else if constexpr (R == 3) dft3<INV>(v[0], v[1], v[2]);
+  else if constexpr (R == 4) dft4<INV>(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+}
+
+// exact small-integer quotient for q < 2^20: floor((x + 0.5) * rcp)
+__device__ __forceinline__ int fquot(int x, float rcp) { return __float2int_rz((float(x) + 0.5f) * rcp); }
+
+// One radix-R Stockham stage over the whole tile, in place. Every thread
+// owns E/R butterflies; all inputs are staged in registers before the
+// barrier so the stage can overwrite its input.
+//   input  index of butterfly (j, r): j + r*L/R
+//   output index:                     (j - k)*R + k + r*ns,  k = j mod ns
+template <typename C, int E, int R, bool INV>
+__device__ __forceinline__ void fft_stage(C* s, int ld, int L, const FftStage& sg, const C* __restrict__ tw,
+                                          int tid, int nthr) {
+  constexpr int NB = E / R;
+  static_assert(NB * R == E, "radix must divide the per-thread element count");
+  const int lr = L / R;
+  C v[NB][R];
+  int wrow[NB], jj[NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int bi = tid + b * nthr;
+    const int w = fquot(bi, sg.rcp_lr);
+    const int j = bi - w * lr;
+    wrow[b] = w;
+    jj[b] = j;
+    const C* src = s + w * ld;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[b][r] = src[phys(j + r * lr)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const int j = jj[b];
+    const int k = j - sg.ns * fquot(j, sg.rcp_ns);
+    if (sg.ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C w = tw[r * k * sg.tw_step];
+        v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+      }
+    }
+    dft<R, INV>(v[b]);
+    C* dst = s + wrow[b] * ld;
+    const int o = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[phys(o + r * sg.ns)] = v[b][r];
+  }
+  __syncthreads();
+}
+
+// Full length-L transform of every row of the tile (natural order in and out).
+template <typename C, int E, bool INV>
+__device__ __forceinline__ void fft_tile(C* s, int ld, const FftPlan& p, int tid, int nthr) {
+  const C* tw = reinterpret_cast<const C*>(p.tw);
+  for (int q = 0; q < p.nst; ++q) {
+    const FftStage& sg = p.st[q];
+    switch (sg.radix) {
+      case 2: if constexpr (E % 2 == 0) fft_stage<C, E, 2, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
+      case 3: if constexpr (E % 3 == 0) fft_stage<C, E, 3, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
+      case 4: if constexpr (E % 4 == 0) fft_stage<C, E, 4, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
+      case 8: if constexpr (E % 8 == 0) fft_stage<C, E, 8, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
+      case 16: if constexpr (E % 16 == 0) fft_stage<C, E, 16, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
+      default: break;
+    }
+  }
+}
+
+}  // namespace gad

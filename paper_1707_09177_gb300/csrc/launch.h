@@ -1,0 +1,24 @@
+// Host-side launchers for the pass kernels, instantiated per precision in
+// kernels_f32.cu and kernels_f64.cu (compiled in parallel).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "args.h"
+
+namespace gad {
+
+enum PassKind : int { PK_XFWD = 0, PK_XINV = 1, PK_FILT = 2, PK_YFWD = 3, PK_YINV = 4 };
+
+// Launches pass `kind` with per-thread element count E (16 or 24). Returns the
+// launch error (cudaSuccess when enqueued).
+template <typename T>
+cudaError_t launch_pass(int kind, int E, dim3 grid, int threads, size_t smem, cudaStream_t s,
+                        const PassArgs<T>& a);
+
+template <typename T>
+cudaError_t launch_cg_finish(T* u, const T* p, const FieldState* st, long long P, int batch, cudaStream_t s);
+
+cudaError_t launch_reset_state(FieldState* st, int batch, cudaStream_t s);
+
+}  // namespace gad
