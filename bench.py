@@ -1,0 +1,392 @@
+"""Benchmark: deconvolved Mpoints/s to relative residual 1e-6 on one GB300
+(or N GPUs, one process each, weak scaling: every rank solves its own batch).
+
+Workload (default): 16 seeded 2048^2 float32 fields with a k^-3 spectrum
+(k_p = 10, exp(-(k/600)^2) cutoff), filtered with the Germano elliptic filter
+at gamma = 0.01, deconvolved by BiCGSTAB to h <= 1e-6 with float64 dots and
+scalars. One step = one solve of the batch (a single library call); the inputs
+(256 MiB) are larger than L2, so no flush is needed between steps. The JSON
+line also reports CG and Van Cittert on the same batch, the roofline of the
+dominant pass kernel, the oracle timed on the host cores, and clocks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--method bicgstab]
+    python bench.py --impl reference     # the CPU oracle, bounded samples
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(name="scalar2d_2048_f32_x16", shape=(2048, 2048), batch=16, gamma=0.01, tol=1e-6,
+                kp=10.0, kcut=600.0)
+METRIC = "deconvolved Mpoints/s to 1e-6 rel. residual"
+UNIT = "Mpoints/s"
+VC_MAXIT = 2000
+
+
+def _spectrum(k):
+    from synth import fields
+    return fields.spectrum_2d_kraichnan(k, kp=WORKLOAD["kp"], kcut=WORKLOAD["kcut"])
+
+
+def _fields(seeds):
+    from synth import fields
+    n = WORKLOAD["shape"]
+    out = np.empty((len(seeds),) + tuple(n), dtype=np.float32)
+    for i, s in enumerate(seeds):
+        out[i] = fields.random_scalar_field(n, s, _spectrum)
+    return out
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("fft.cuh", "passes.cuh", "args.h"):
+        with open(os.path.join(ROOT, "paper_1707_09177_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) of SM clocks and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    c = [x.strip() for x in line.split(",")]
+                    if len(c) < 9:
+                        continue
+                    try:
+                        sm.append(float(c[1]))
+                        mx = max(mx, float(c[2]))
+                    except ValueError:
+                        continue
+                    for n, v in zip(names, c[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(n)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _pass_bytes(kind, op, P, SP, B, method):
+    """Algorithmic bytes one launch must move (each array read or written
+    once), float32 fields (4 B) and complex64 spectra (8 B)."""
+    v, s = 4 * P * B, 8 * SP * B
+    if kind == "filt":
+        return 2 * s                                   # spectrum in, filtered spectrum out
+    if kind == "xfwd":
+        rw = {0: (1, 0), 1: (2, 1), 2: (3, 2), 3: (3, 1), 4: (2, 1)}[op]  # (vectors read, written)
+        return (rw[0] + rw[1]) * v + s
+    if kind == "xinv":
+        rw = {0: (0, 1), 1: (1, 1), 2: (1, 0), 3: (1, 1), 4: (1, 1), 5: (2, 2), 6: (1, 1), 7: (4, 2)}[op]
+        return s + (rw[0] + rw[1]) * v
+    return 2 * s
+
+
+def _oracle_solve_seconds(ub64, gamma, method, passes):
+    """Wall time of one oracle solve with a fixed number of passes (includes
+    the initial residual and the final true-residual check)."""
+    import oracle
+    t = time.perf_counter()
+    oracle.solve(method, ub64, gamma, tol=0.0, maxit=passes)
+    return time.perf_counter() - t
+
+
+def _oracle_estimate(ub64, gamma, method, n_target, sample_passes):
+    """Seconds of a full oracle solve of n_target passes, from a bounded
+    sample: fixed cost (0 passes) plus n_target times the per-pass cost."""
+    t0 = _oracle_solve_seconds(ub64, gamma, method, 0)
+    tk = _oracle_solve_seconds(ub64, gamma, method, sample_passes)
+    per = max(tk - t0, 1e-9) / sample_passes
+    return t0 + n_target * per, per, t0
+
+
+def _golden_count(method, seed):
+    p = os.path.join(ROOT, "tests", "golden", "counts_2048.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    for r in d["runs"]:
+        if r["method"] == method and r["precision"] == "f64" and r["seed"] == seed:
+            return int(r["iterations"])
+    return None
+
+
+def run_reference(args):
+    """The CPU oracle timed on the host cores: each step is one BiCGSTAB pass
+    over one 2048^2 field; the metric extrapolates the per-pass time to the
+    oracle's own iteration count for that field (tests/golden/counts_2048.json)."""
+    ws, rank, _ = _dist()
+    if ws > 1 and rank != 0:
+        return
+    os.environ["OMP_NUM_THREADS"] = "1"
+    import oracle
+    ub = oracle.filter_field(_fields([0])[0].astype(np.float64), WORKLOAD["gamma"])
+    ub = ub.astype(np.float32).astype(np.float64)
+    g = WORKLOAD["gamma"]
+    for _ in range(args.warmup):
+        _oracle_solve_seconds(ub, g, args.method, 1)
+    t0 = _oracle_solve_seconds(ub, g, args.method, 0)
+    ts = [_oracle_solve_seconds(ub, g, args.method, 1) for _ in range(args.steps)]
+    per = max(float(np.mean(ts)) - t0, 1e-9)
+    n_iter = _golden_count(args.method, 0) or 160
+    P = WORKLOAD["shape"][0] * WORKLOAD["shape"][1]
+    t_solve = t0 + n_iter * per
+    value = P / t_solve / 1e6
+    sample = ("oracle %s (float64 NumPy, 1 thread), one 2048^2 field (seed 0): %d timed one-pass solves after %d "
+              "warm-up, minus the fixed cost of a zero-pass solve; Mpoints/s = P / (fixed + %d passes x %.2f s), "
+              "%d = the oracle's own pass count to 1e-6 for that field"
+              % (args.method, args.steps, args.warmup, n_iter, per, n_iter))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "method": args.method},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "cg", "vancittert", "sd"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the comparison methods and CPU baseline")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the iteration loop from the host instead of a graph while node (same kernels; "
+                         "profilers cannot see kernel nodes of graphs with conditional nodes)")
+    ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="fields per GPU")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_1707_09177_gb300 as gad
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    B, gamma, tol = args.batch, WORKLOAD["gamma"], WORKLOAD["tol"]
+    n = WORKLOAD["shape"]
+    P = n[0] * n[1]
+    seeds = list(range(rank * B, rank * B + B))
+    gad.load()
+    if args.host_loop:
+        gad.set_graph_mode(False)
+
+    # inputs: true fields from the seeded generator, filtered by the library
+    u_true = torch.from_numpy(_fields(seeds)).to(dev)
+    ubar = gad.filter(u_true, gamma, ndim=2)
+    del u_true
+    ubar_host = ubar.cpu().pin_memory()
+    out = torch.empty_like(ubar)
+    stream = torch.cuda.current_stream()
+
+    def step(method, maxit=3000, tol_=tol):
+        return gad.deconvolve(ubar, gamma, method=method, tol=tol_, maxit=maxit, ndim=2, out=out)
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        res = step(args.method)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step(args.method)
+            launches += res.launches
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    clocks = clk.summary()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = ws * B * P / (ms * 1e-3) / 1e6
+    iters = [int(x) for x in res.iterations]
+    ok = bool(np.all(res.status == gad.AD_OK))
+
+    # end to end through the public API with host buffers
+    host_out = torch.empty(ubar.shape, dtype=ubar.dtype).pin_memory()
+    dev_in = torch.empty_like(ubar)
+
+    def e2e_step():
+        dev_in.copy_(ubar_host, non_blocking=True)
+        r = gad.deconvolve(dev_in, gamma, method=args.method, tol=tol, maxit=3000, ndim=2, out=out)
+        host_out.copy_(out, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+        return r
+
+    e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = ubar.numel() * ubar.element_size()
+    e2e = {"value": ws * B * P / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "grid": "2048x2048", "batch_per_gpu": B, "gamma": gamma,
+                       "tol": tol, "method": args.method, "dots": "f64 (compensated f32 products)",
+                       "l2": "inputs %d MiB per vector, > L2 at batch 16; no flush" % (B * P * 4 >> 20),
+                       "loop": "host" if args.host_loop else "graph while node",
+                       "parallelism": "replicas" if ws > 1 else "1 gpu"},
+            "iterations": {"min": min(iters), "max": max(iters), "mean": float(np.mean(iters))},
+            "converged": ok, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
+
+    if rank == 0 and not args.no_extras:
+        # comparison methods on the same batch (one timed solve each)
+        methods = {}
+        for m, mi in (("cg", 3000), ("bicgstab", 3000), ("vancittert", VC_MAXIT)):
+            step(m, maxit=mi)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            r = step(m, maxit=mi)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            t = ev0.elapsed_time(ev1)
+            its = [int(x) for x in r.iterations]
+            reached = bool(np.all(r.status == gad.AD_OK))
+            hfin = [float(r.history[b, its[b]]) for b in range(B)]
+            methods[m] = {"ms": t, "iterations_mean": float(np.mean(its)), "reached_tol": reached,
+                          "mpoints_s": B * P / (t * 1e-3) / 1e6 if reached else None,
+                          "mpoints_s_per_pass": B * P * float(np.mean(its)) / (t * 1e-3) / 1e6,
+                          "h_final_max": max(hfin)}
+            if m == "vancittert":
+                methods[m]["maxit"] = VC_MAXIT
+        line["methods"] = methods
+
+        # roofline of the dominant pass kernel, timed live with CUDA events
+        passes = gad.time_passes(n, gamma, B, method=args.method, reps=20)
+        kxn = n[1] // 2 + 1
+        SP = kxn * n[0]
+        best = max(passes, key=lambda p: p["ms"])
+        total = sum(p["ms"] for p in passes)
+        peak, src = _peaks()
+        for p in passes:
+            p["bytes"] = _pass_bytes(p["kind"], p["op"], P, SP, B, args.method)
+            p["gbs"] = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+        traffic = None
+        tp = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tp):
+            with open(tp) as f:
+                td = json.load(f)
+            k = "%s:%d" % (best["kind"], best["op"])
+            if td.get("kernel_sha") == _kernel_sha() and k in td.get("bytes_per_launch", {}):
+                traffic = td["bytes_per_launch"][k]
+        line["roofline"] = {"bound": "hbm", "kernel": "%s(op %d)" % (best["kind"], best["op"]),
+                            "achieved": best["gbs"], "peak": peak, "unit": "GB/s", "frac": best["gbs"] / peak,
+                            "peak_source": src + " hbm_gbs (copy, burst)", "traffic": traffic,
+                            "share_of_iteration": best["ms"] / total,
+                            "passes": [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in passes]}
+
+        # the oracle on this host's cores, bounded sample
+        os.environ["OMP_NUM_THREADS"] = "1"
+        import oracle
+        ub0 = ubar_host[0].numpy().astype(np.float64)
+        sample_passes = 4
+        n0 = iters[0]
+        t_solve, per, t0 = _oracle_estimate(ub0, gamma, args.method, n0, sample_passes)
+        cpu_val = P / t_solve / 1e6
+        line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": ("oracle %s (float64 NumPy, 1 thread), field 0 of the batch: a 0-pass "
+                                           "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
+                                           "extrapolated to the %d passes the GPU solve of that field needed"
+                                           % (args.method, t0, sample_passes, per, n0))}
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -106,6 +106,21 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
                         const void* u0, int* iterations, ad_status* status,
                         double* res_hist, double* true_res, void* stream);
 
+/* Measures one pass kernel of an iteration of `method` for this grid and
+ * batch: the kernel is launched once to warm up, then `reps` times back to
+ * back on `stream` between two CUDA events, in exactly the launch shape and
+ * fused prologue/epilogue a solve uses, but on the context's internal
+ * buffers (caller memory is never touched) and with every field forced
+ * active and no scalar update. `index` selects the launch within the
+ * iteration body (0 .. count-1, in launch order); index = -1 only reports
+ * the count. Outputs (host, may be NULL): ms_per_launch, kind (0 forward x,
+ * 1 inverse x, 2 filter, 3 forward y, 4 inverse y), op (the fused
+ * prologue/epilogue/dot code of that pass), count (launches per iteration).
+ * Blocks the host until the timing completes. No counterpart in the paper:
+ * it exists to relate measured kernel time to the HBM roofline. */
+ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method method, int index, int reps,
+                       void* stream, double* ms_per_launch, int* kind, int* op, int* count);
+
 /* Enables (1, default) or disables (0) capture of each solve into one CUDA
  * graph whose iteration loop is a device-side conditional while node. With 0
  * the host launches the iteration body in chunks and polls the device

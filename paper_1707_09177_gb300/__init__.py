@@ -30,8 +30,9 @@ AD_ERR_ARG, AD_ERR_NONFINITE, AD_ERR_CUDA, AD_ERR_TIMEOUT, AD_ERR_NOMEM = -1, -2
 METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3}
 AD_F32, AD_F64 = 0, 1
 
-EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_set_graph_mode",
+EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_time_pass", "ad_set_graph_mode",
             "ad_last_launch_count", "ad_status_str", "ad_last_error")
+PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv"}
 
 
 class ad_grid(ctypes.Structure):
@@ -74,6 +75,8 @@ def load(path=None):
     lib.ad_deconvolve.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_i, c_d, c_i, c_p,
                                   c_p, c_p, c_p, c_p, c_p]
     lib.ad_deconvolve.restype = c_i
+    lib.ad_time_pass.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_i, c_i, c_p, c_p, c_p, c_p, c_p]
+    lib.ad_time_pass.restype = c_i
     lib.ad_set_graph_mode.argtypes = [c_p, c_i]
     lib.ad_set_graph_mode.restype = c_i
     lib.ad_last_launch_count.argtypes = [c_p]
@@ -201,3 +204,30 @@ def deconvolve(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, u0=None, nd
     _check(st, ctx, per_field=True)
     return Solve(u=out, iterations=its, status=sts, history=hist, true_residual=tr,
                  launches=int(lib.ad_last_launch_count(ctx)))
+
+
+def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, stream=None, device=None):
+    """Per-launch time (ms) of every pass kernel of one iteration of ``method``,
+    measured by the library with CUDA events in the solve's launch shapes.
+    Returns a list of dicts (index, kind, op, ms)."""
+    lib = load()
+    ctx = context(device)
+    g = ad_grid()
+    g.ndim = len(shape)
+    rev = list(reversed(shape)) + [1] * (3 - len(shape))
+    for i in range(3):
+        g.n[i] = int(rev[i])
+    g.dtype = AD_F32 if dtype == "f32" else AD_F64
+    g.gamma = float(gamma)
+    cnt = ctypes.c_int(0)
+    st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), METHODS[method], -1, 1, _stream_ptr(stream),
+                          None, None, None, ctypes.byref(cnt))
+    _check(st, ctx)
+    out = []
+    for i in range(cnt.value):
+        ms, kind, op = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), METHODS[method], i, int(reps), _stream_ptr(stream),
+                              ctypes.byref(ms), ctypes.byref(kind), ctypes.byref(op), None)
+        _check(st, ctx)
+        out.append(dict(index=i, kind=PASS_KINDS[kind.value], op=int(op.value), ms=float(ms.value)))
+    return out

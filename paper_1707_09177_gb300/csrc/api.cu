@@ -61,6 +61,7 @@ struct Plan {
   const void* twx = nullptr;
   void *S1 = nullptr, *S2 = nullptr;
   void *R = nullptr, *Pv = nullptr, *Q = nullptr, *Sv = nullptr, *F0 = nullptr;
+  void* Uscratch = nullptr;          // stands in for u when a single pass is timed
   FieldState* st = nullptr;
   double* part = nullptr;
   unsigned* ticket = nullptr;
@@ -77,7 +78,17 @@ struct GraphEntry {
 
 }  // namespace
 
+struct LaunchRec {
+  int kind = 0, E = 0, threads = 0;
+  dim3 grid;
+  size_t smem = 0;
+  bool f64 = false;
+  PassArgs<float> af{};
+  PassArgs<double> ad{};
+};
+
 struct ad_ctx {
+  std::vector<LaunchRec>* record = nullptr;   // when set, pass launches are recorded, not issued
   int device = 0;
   cudaStream_t cap = nullptr, cap2 = nullptr;
   bool use_graph = true;
@@ -367,7 +378,7 @@ PassArgs<T> base_args(const Plan* p, const Common& c) {
   a.twx = p->twx;
   const double kc = p->gamma * (double)std::min(p->nx, std::min(p->ny, p->ndim == 3 ? p->nz : p->ny)) / 2.0;
   a.kc2 = (T)(kc * kc);
-  a.inv_p = 1.0 / (double)p->P;
+  a.inv_p = 1.0;                      // physical-space dots are plain sums
   a.gscale = (T)(1.0 / (double)p->P);
   a.S1 = p->S1; a.S2 = p->S2;
   a.st = c.st; a.cfg = c.cfg; a.part = p->part; a.ticket = p->ticket;
@@ -377,7 +388,26 @@ PassArgs<T> base_args(const Plan* p, const Common& c) {
 
 template <typename T>
 void set_pass(PassArgs<T>& a, const PassCfg& pc) {
-  a.W = pc.W; a.ld = pc.ld; a.fft = pc.fft; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b;
+  a.W = pc.W; a.ld = pc.ld; a.fft = pc.fft; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b; a.tfft = pc.T;
+}
+
+// Blocks always hold whole warps (the reductions shuffle over full warps).
+int block_threads(const PassCfg& pc) { return (pc.T + 31) / 32 * 32; }
+
+template <typename T> void store_args(LaunchRec& r, const PassArgs<T>& a);
+template <> void store_args<float>(LaunchRec& r, const PassArgs<float>& a) { r.af = a; r.f64 = false; }
+template <> void store_args<double>(LaunchRec& r, const PassArgs<double>& a) { r.ad = a; r.f64 = true; }
+
+template <typename T>
+cudaError_t issue(ad_ctx* ctx, int kind, const PassCfg& pc, cudaStream_t s, const PassArgs<T>& a) {
+  if (ctx->record) {
+    LaunchRec r;
+    r.kind = kind; r.E = pc.E; r.grid = pc.grid; r.threads = block_threads(pc); r.smem = pc.smem;
+    store_args<T>(r, a);
+    ctx->record->push_back(r);
+    return cudaSuccess;
+  }
+  return launch_pass<T>(kind, pc.E, pc.grid, block_threads(pc), pc.smem, s, a);
 }
 
 template <typename T>
@@ -389,11 +419,11 @@ ad_status enqueue_G(ad_ctx* ctx, Plan* p, cudaStream_t s, const Fwd& fw, const F
   a.op = fw.op; a.A = (const T*)fw.A; a.B = (const T*)fw.B;
   a.O1 = (T*)fw.O1; a.O2 = (T*)fw.O2; a.O3 = (T*)fw.O3;
   a.ndots = 0; a.stage = SS_NONE; a.set_cond = 0; a.clear_cond = (fw.clear_cond && c.in_graph) ? 1 : 0;
-  CK(launch_pass<T>(PK_XFWD, p->xf.E, p->xf.grid, p->xf.T, p->xf.smem, s, a));
+  CK(issue<T>(ctx, PK_XFWD, p->xf, s, a));
   ++*nl;
   if (p->ndim == 3) {
     set_pass(a, p->yf);
-    CK(launch_pass<T>(PK_YFWD, p->yf.E, p->yf.grid, p->yf.T, p->yf.smem, s, a));
+    CK(issue<T>(ctx, PK_YFWD, p->yf, s, a));
     ++*nl;
   }
   a.clear_cond = 0;
@@ -401,19 +431,20 @@ ad_status enqueue_G(ad_ctx* ctx, Plan* p, cudaStream_t s, const Fwd& fw, const F
   a.op = fl.op;
   a.ndots = fl.op == FI_NONE ? 0 : (fl.op == FI_XGX ? 1 : 3);
   a.stage = fl.stage;
-  CK(launch_pass<T>(PK_FILT, p->fl.E, p->fl.grid, p->fl.T, p->fl.smem, s, a));
+  a.inv_p = 1.0 / (double)p->P;       // Parseval: (a, b) = (1/P) sum_k a_hat conj(b_hat)
+  CK(issue<T>(ctx, PK_FILT, p->fl, s, a));
   ++*nl;
-  a.ndots = 0; a.stage = SS_NONE;
+  a.ndots = 0; a.stage = SS_NONE; a.inv_p = 1.0;
   if (p->ndim == 3) {
     set_pass(a, p->yi);
-    CK(launch_pass<T>(PK_YINV, p->yi.E, p->yi.grid, p->yi.T, p->yi.smem, s, a));
+    CK(issue<T>(ctx, PK_YINV, p->yi, s, a));
     ++*nl;
   }
   set_pass(a, p->xi);
   a.op = iv.op; a.A = (const T*)iv.A; a.B = (const T*)iv.B; a.C = (const T*)iv.C;
   a.O1 = (T*)iv.O1; a.O2 = (T*)iv.O2; a.O3 = nullptr;
   a.ndots = iv.ndots; a.stage = iv.stage; a.set_cond = (iv.set_cond && c.in_graph) ? 1 : 0;
-  CK(launch_pass<T>(PK_XINV, p->xi.E, p->xi.grid, p->xi.T, p->xi.smem, s, a));
+  CK(issue<T>(ctx, PK_XINV, p->xi, s, a));
   ++*nl;
   return AD_OK;
 }
@@ -647,6 +678,60 @@ void ad_destroy(ad_ctx* c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
   delete c;
+}
+
+ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method method, int index, int reps,
+                       void* stream, double* ms_per_launch, int* kind, int* op, int* count) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 1 || reps < 1 || method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "bad batch, reps or method");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
+  if ((s = ensure_vectors(ctx, p)) != AD_OK) return s;
+  if ((s = ensure_hist(ctx, p, 1)) != AD_OK) return s;
+  if (!p->Uscratch && (s = dmalloc(ctx, p, &p->Uscratch, (size_t)p->P * p->batch * (p->f64 ? 8 : 4))) != AD_OK) return s;
+  // record one iteration body on internal buffers only
+  std::vector<LaunchRec> rec;
+  ctx->record = &rec;
+  Common c;
+  c.st = p->st;
+  c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method; c.cfg.hist = p->hist; c.cfg.hist_ld = p->hist_cap;
+  SolveIO io{p->F0, p->Uscratch, nullptr, (int)method, false};
+  int nl = 0;
+  s = p->f64 ? enqueue_body<double>(ctx, p, nullptr, io, c, &nl) : enqueue_body<float>(ctx, p, nullptr, io, c, &nl);
+  ctx->record = nullptr;
+  if (s != AD_OK) return s;
+  if (count) *count = (int)rec.size();
+  if (index < 0 || index >= (int)rec.size()) return index < 0 ? AD_OK : fail(ctx, AD_ERR_ARG, "pass index out of range");
+  LaunchRec r = rec[index];
+  // every field computes, no scalar update, no graph condition
+  r.af.force = r.ad.force = 1;
+  r.af.stage = r.ad.stage = SS_NONE;
+  r.af.set_cond = r.ad.set_cond = 0;
+  r.af.clear_cond = r.ad.clear_cond = 0;
+  if (kind) *kind = r.kind;
+  if (op) *op = r.f64 ? r.ad.op : r.af.op;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto go = [&]() { return r.f64 ? launch_pass<double>(r.kind, r.E, r.grid, r.threads, r.smem, st, r.ad)
+                                  : launch_pass<float>(r.kind, r.E, r.grid, r.threads, r.smem, st, r.af); };
+  cudaError_t e = go();                              // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = go();
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ad_time_pass");
+  if (ms_per_launch) *ms_per_launch = (double)ms / reps;
+  ctx->launches = reps + 1;
+  return AD_OK;
 }
 
 ad_status ad_set_graph_mode(ad_ctx* c, int enable) {

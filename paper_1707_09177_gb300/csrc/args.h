@@ -59,12 +59,14 @@ struct PassArgs {
   long long P;               // real points per field
   long long SP;              // complex points per spectral buffer per field
   int W, ld;                 // tile width (sequences per block), smem row stride
+  int tfft;                  // threads that run FFT butterflies (W*L/E); blockDim.x is
+                             // this rounded up to a multiple of 32
   float rcp_a;               // reciprocal helpers for index splits (see kernels)
   float rcp_b;
   FftPlan fft;               // transform along this pass's axis
   const void* twx;           // exp(-2 pi i m / nx) table for the real-FFT split
   T kc2;                     // k_c^2
-  double inv_p;              // 1/P (Parseval scale of the dots)
+  double inv_p;              // scale of the block dots: 1/P for Parseval sums, else 1
   T gscale;                  // 1/P folded into the filter multiply
   void* S1;
   void* S2;

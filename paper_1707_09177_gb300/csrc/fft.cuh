@@ -154,18 +154,22 @@ __device__ __forceinline__ void fft_stage(C* s, int ld, int L, const FftStage& s
   const int lr = L / R;
   C v[NB][R];
   int wrow[NB], jj[NB];
+  const bool on = tid < nthr;     // threads beyond the FFT's thread count only join barriers
+  if (on) {
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int bi = tid + b * nthr;
-    const int w = fquot(bi, sg.rcp_lr);
-    const int j = bi - w * lr;
-    wrow[b] = w;
-    jj[b] = j;
-    const C* src = s + w * ld;
+    for (int b = 0; b < NB; ++b) {
+      const int bi = tid + b * nthr;
+      const int w = fquot(bi, sg.rcp_lr);
+      const int j = bi - w * lr;
+      wrow[b] = w;
+      jj[b] = j;
+      const C* src = s + w * ld;
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[b][r] = src[phys(j + r * lr)];
+      for (int r = 0; r < R; ++r) v[b][r] = src[phys(j + r * lr)];
+    }
   }
   __syncthreads();
+  if (on) {
 #pragma unroll
   for (int b = 0; b < NB; ++b) {
     const int j = jj[b];
@@ -183,10 +187,12 @@ __device__ __forceinline__ void fft_stage(C* s, int ld, int L, const FftStage& s
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[phys(o + r * sg.ns)] = v[b][r];
   }
+  }
   __syncthreads();
 }
 
 // Full length-L transform of every row of the tile (natural order in and out).
+// nthr is the FFT's logical thread count (W*L/E); the block may be larger.
 template <typename C, int E, bool INV>
 __device__ __forceinline__ void fft_tile(C* s, int ld, const FftPlan& p, int tid, int nthr) {
   const C* tw = reinterpret_cast<const C*>(p.tw);

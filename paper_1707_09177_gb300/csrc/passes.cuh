@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(512) k_xfwd(PassArgs<T> a) {
     row[phys(2 * q + 1)] = C{x.v[2], x.v[3]};
   }
   __syncthreads();
-  fft_tile<C, E, false>(s, a.ld, a.fft, tid, nthr);
+  fft_tile<C, E, false>(s, a.ld, a.fft, tid, a.tfft);
   // split the packed half-length transform into the real-input spectrum
   const C* twx = reinterpret_cast<const C*>(a.twx);
   const int h1 = (M >> 1) + 1;
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(512) k_xinv(PassArgs<T> a) {
       }
     }
     __syncthreads();
-    fft_tile<C, E, true>(s, a.ld, a.fft, tid, nthr);
+    fft_tile<C, E, true>(s, a.ld, a.fft, tid, a.tfft);
     const long long base = (long long)f * a.P + (long long)row0 * nx;
     const T al = st ? T(st->alpha) : T(0), om = st ? T(st->omega) : T(0);
     for (int idx = tid; idx < a.W * cpr; idx += nthr) {
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(512) k_filt(PassArgs<T> a) {
       row[phys(2 * i2 + 1)] = v1;
     }
     __syncthreads();
-    fft_tile<C, E, false>(s, a.ld, a.fft, tid, nthr);
+    fft_tile<C, E, false>(s, a.ld, a.fft, tid, a.tfft);
     const int nxh = a.nx >> 1;
     for (int idx = tid; idx < a.W * L; idx += nthr) {
       const int w = fquot(idx, a.rcp_b);
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(512) k_filt(PassArgs<T> a) {
       *pv = C{X.x * sc, X.y * sc};
     }
     __syncthreads();
-    fft_tile<C, E, true>(s, a.ld, a.fft, tid, nthr);
+    fft_tile<C, E, true>(s, a.ld, a.fft, tid, a.tfft);
     for (int idx = tid; idx < a.W * half; idx += nthr) {
       const int w = fquot(idx, a.rcp_a);
       const int i2 = idx - w * half;
@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(512) k_yfwd(PassArgs<T> a) {
     row[phys(2 * i2 + 1)] = src[1];
   }
   __syncthreads();
-  fft_tile<C, E, false>(s, a.ld, a.fft, tid, nthr);
+  fft_tile<C, E, false>(s, a.ld, a.fft, tid, a.tfft);
   C* S2 = reinterpret_cast<C*>(a.S2) + (long long)f * a.SP + (long long)kx * L * a.nz + z0;
   const int lw = __ffs(a.W) - 1;
   for (int idx = tid; idx < a.W * L; idx += nthr) {
@@ -609,7 +609,7 @@ __global__ void __launch_bounds__(512) k_yinv(PassArgs<T> a) {
     s[w * a.ld + phys(ky)] = S2[(long long)ky * a.nz + w];
   }
   __syncthreads();
-  fft_tile<C, E, true>(s, a.ld, a.fft, tid, nthr);
+  fft_tile<C, E, true>(s, a.ld, a.fft, tid, a.tfft);
   C* S1 = reinterpret_cast<C*>(a.S1) + (long long)f * a.SP;
   for (int idx = tid; idx < a.W * half; idx += nthr) {
     const int w = fquot(idx, a.rcp_a);

@@ -73,7 +73,7 @@ def test_filter_full_size_batch_sampled(gad):
     batch, n = 16, 2048
     u = torch.empty((batch, n, n), dtype=torch.float32, device="cuda")
     u.copy_(torch.from_numpy(rng.standard_normal((batch, n, n)).astype(np.float32)))
-    out = gad.filter(u, 0.01).cpu().numpy()
+    out = gad.filter(u, 0.01, ndim=2).cpu().numpy()
     uh = u.cpu().numpy()
     for b in (0, 7, 15):
         ref = oracle.filter_field(uh[b].astype(np.float64), 0.01)
