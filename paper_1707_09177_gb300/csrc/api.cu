@@ -13,6 +13,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -48,6 +49,7 @@ struct PassCfg {
   int E = 0, W = 0, T = 0, ld = 0;
   size_t smem = 0;
   FftPlan fft{};
+  FftPlan fft_inv{};
   float rcp_a = 0.f, rcp_b = 0.f;
   dim3 grid;
 };
@@ -181,9 +183,8 @@ bool radices_for(int L, int E, std::vector<int>& rad) {
   return true;
 }
 
-bool make_fft(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
-  std::vector<int> rad;
-  if (!radices_for(L, E, rad) || rad.size() > 8) return false;
+bool make_fft_from(int L, const std::vector<int>& rad, const void* tab, long long Ltab, FftPlan& fp) {
+  if (rad.empty() || rad.size() > 5) return false;     // the kernels unroll at most 5 stages
   fp = FftPlan{};
   fp.L = L;
   fp.nst = (int)rad.size();
@@ -201,6 +202,20 @@ bool make_fft(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
   return ns == L;
 }
 
+bool make_fft(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
+  std::vector<int> rad;
+  return radices_for(L, E, rad) && make_fft_from(L, rad, tab, Ltab, fp);
+}
+
+// The same radices in reverse order: the filter pass's inverse transform,
+// whose first stage meets the forward transform's last stage in registers.
+bool make_fft_reversed(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
+  std::vector<int> rad;
+  if (!radices_for(L, E, rad)) return false;
+  std::reverse(rad.begin(), rad.end());
+  return make_fft_from(L, rad, tab, Ltab, fp);
+}
+
 // Picks the tile width W (a power of two dividing `div`, or any power of two
 // when div = 0) and the block size T = W*L/E closest to 256 threads.
 bool choose_tile(int L, int E, int slots, int div, size_t csize, PassCfg& pc) {
@@ -213,7 +228,7 @@ bool choose_tile(int L, int E, int slots, int div, size_t csize, PassCfg& pc) {
     const long long tot = (long long)W * L;
     if (tot % E != 0) continue;
     const long long T = tot / E;
-    if (T < 1 || T > 512) continue;
+    if (T < 1 || T > 256) continue;
     const size_t smem = (size_t)W * ld * csize;
     if (smem > 100 * 1024) continue;
     const double score = std::fabs(std::log2((double)T / 256.0));
@@ -301,6 +316,7 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
   const int nseq = p->ndim == 3 ? p->kxn * p->ny : p->kxn;
   ok = ok && choose_tile(Lf, pick_E(Lf), Lf, 0, cs, p->fl);
   ok = ok && make_fft(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft);
+  ok = ok && make_fft_reversed(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft_inv);
   p->fl.rcp_a = 1.0f / (float)(Lf / 2);
   p->fl.rcp_b = 1.0f / (float)Lf;
   p->fl.grid = dim3((nseq + std::max(p->fl.W, 1) - 1) / std::max(p->fl.W, 1), batch);
@@ -319,8 +335,11 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
   const unsigned maxblk = std::max(p->xi.grid.x, p->fl.grid.x);
   if ((s = dmalloc(ctx, p, (void**)&p->st, sizeof(FieldState) * batch)) != AD_OK ||
       (s = dmalloc(ctx, p, (void**)&p->part, sizeof(double) * 4 * maxblk * batch)) != AD_OK ||
-      (s = dmalloc(ctx, p, (void**)&p->ticket, 64)) != AD_OK) { free_plan(p); return s; }
-  if (cudaMemset(p->ticket, 0, 64) != cudaSuccess) { free_plan(p); return cuda_fail(ctx, cudaGetLastError(), "ticket"); }
+      (s = dmalloc(ctx, p, (void**)&p->ticket, sizeof(unsigned) * (4 + batch))) != AD_OK) { free_plan(p); return s; }
+  if (cudaMemset(p->ticket, 0, sizeof(unsigned) * (4 + batch)) != cudaSuccess) {
+    free_plan(p);
+    return cuda_fail(ctx, cudaGetLastError(), "ticket");
+  }
   (void)vb;
   ctx->plans[key] = p;
   *out = p;
@@ -388,7 +407,8 @@ PassArgs<T> base_args(const Plan* p, const Common& c) {
 
 template <typename T>
 void set_pass(PassArgs<T>& a, const PassCfg& pc) {
-  a.W = pc.W; a.ld = pc.ld; a.fft = pc.fft; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b; a.tfft = pc.T;
+  a.W = pc.W; a.ld = pc.ld; a.fft = pc.fft; a.fft_inv = pc.fft_inv; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b;
+  a.tfft = pc.T;
 }
 
 // Blocks always hold whole warps (the reductions shuffle over full warps).

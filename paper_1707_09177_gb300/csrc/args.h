@@ -64,6 +64,7 @@ struct PassArgs {
   float rcp_a;               // reciprocal helpers for index splits (see kernels)
   float rcp_b;
   FftPlan fft;               // transform along this pass's axis
+  FftPlan fft_inv;           // filter pass: the same radices in reverse order
   const void* twx;           // exp(-2 pi i m / nx) table for the real-FFT split
   T kc2;                     // k_c^2
   double inv_p;              // scale of the block dots: 1/P for Parseval sums, else 1
@@ -81,7 +82,7 @@ struct PassArgs {
   FieldState* st;            // nullptr for plain filtering
   SolveConfig cfg;
   double* part;              // [batch][gridDim.x][4] block partial dots
-  unsigned* ticket;          // arrival counter (reset by the last block)
+  unsigned* ticket;          // [0] fields done, [1] loop passes, [2 + f] blocks of field f
   int stage;                 // ScalarStage run by the last block
   int set_cond;              // last block sets the graph's while-condition
   cudaGraphConditionalHandle cond;

@@ -141,14 +141,19 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* v)
 // exact small-integer quotient for q < 2^20: floor((x + 0.5) * rcp)
 __device__ __forceinline__ int fquot(int x, float rcp) { return __float2int_rz((float(x) + 0.5f) * rcp); }
 
-// One radix-R Stockham stage over the whole tile, in place. Every thread
-// owns E/R butterflies; all inputs are staged in registers before the
-// barrier so the stage can overwrite its input.
+// One radix-R Stockham stage over the whole tile. Every thread owns E/R
+// butterflies; all inputs are held in registers before any output is
+// written, so a stage may overwrite its own input.
 //   input  index of butterfly (j, r): j + r*L/R
 //   output index:                     (j - k)*R + k + r*ns,  k = j mod ns
-template <typename C, int E, int R, bool INV>
-__device__ __forceinline__ void fft_stage(C* s, int ld, int L, const FftStage& sg, const C* __restrict__ tw,
-                                          int tid, int nthr) {
+// `load(w, i)` returns input element i of sequence w and `emit(w, i, x)`
+// consumes output element i: shared-memory rows for inner stages, global
+// memory (with the fused Krylov prologue/epilogue) for the first and last
+// stage. `mid_barrier` separates the loads from the writes when both touch
+// the same shared-memory tile.
+template <typename C, int E, int R, bool INV, class Load, class Emit>
+__device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __restrict__ tw, int tid, int nthr,
+                                         Load& load, Emit& emit, bool mid_barrier) {
   constexpr int NB = E / R;
   static_assert(NB * R == E, "radix must divide the per-thread element count");
   const int lr = L / R;
@@ -163,50 +168,185 @@ __device__ __forceinline__ void fft_stage(C* s, int ld, int L, const FftStage& s
       const int j = bi - w * lr;
       wrow[b] = w;
       jj[b] = j;
-      const C* src = s + w * ld;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[b][r] = src[phys(j + r * lr)];
+      for (int r = 0; r < R; ++r) v[b][r] = load(w, j + r * lr);
     }
   }
-  __syncthreads();
+  if (mid_barrier) __syncthreads();
   if (on) {
 #pragma unroll
-  for (int b = 0; b < NB; ++b) {
-    const int j = jj[b];
-    const int k = j - sg.ns * fquot(j, sg.rcp_ns);
-    if (sg.ns > 1) {
+    for (int b = 0; b < NB; ++b) {
+      const int j = jj[b];
+      const int k = j - sg.ns * fquot(j, sg.rcp_ns);
+      if (sg.ns > 1) {
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        C w = tw[r * k * sg.tw_step];
-        v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+        for (int r = 1; r < R; ++r) {
+          const C w = tw[r * k * sg.tw_step];
+          v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
+        }
       }
-    }
-    dft<R, INV>(v[b]);
-    C* dst = s + wrow[b] * ld;
-    const int o = (j - k) * R + k;
+      dft<R, INV>(v[b]);
+      const int o = (j - k) * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[phys(o + r * sg.ns)] = v[b][r];
+      for (int r = 0; r < R; ++r) emit(wrow[b], o + r * sg.ns, v[b][r]);
+    }
   }
-  }
-  __syncthreads();
 }
 
-// Full length-L transform of every row of the tile (natural order in and out).
-// nthr is the FFT's logical thread count (W*L/E); the block may be larger.
-template <typename C, int E, bool INV>
-__device__ __forceinline__ void fft_tile(C* s, int ld, const FftPlan& p, int tid, int nthr) {
-  const C* tw = reinterpret_cast<const C*>(p.tw);
-  for (int q = 0; q < p.nst; ++q) {
-    const FftStage& sg = p.st[q];
-    switch (sg.radix) {
-      case 2: if constexpr (E % 2 == 0) fft_stage<C, E, 2, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
-      case 3: if constexpr (E % 3 == 0) fft_stage<C, E, 3, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
-      case 4: if constexpr (E % 4 == 0) fft_stage<C, E, 4, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
-      case 8: if constexpr (E % 8 == 0) fft_stage<C, E, 8, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
-      case 16: if constexpr (E % 16 == 0) fft_stage<C, E, 16, INV>(s, ld, p.L, sg, tw, tid, nthr); break;
-      default: break;
+// Last forward stage, pointwise spectral multiply, and first inverse stage
+// of the same radix, without leaving registers. The last forward stage
+// (ns = L/R) leaves butterfly j holding X[j + r*L/R] in natural order; an
+// inverse plan whose first radix is R reads exactly those elements for its
+// butterfly j (ns = 1, no twiddles), so the multiply happens in between.
+// `mul(w, i, x)` scales element i and may accumulate inner products;
+// `emit(w, i, x)` consumes the inverse stage's outputs (index j*R + r).
+template <typename C, int E, int R, class Load, class Mul, class Emit>
+__device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C* __restrict__ tw, int tid, int nthr,
+                                             Load& load, Mul& mul, Emit& emit, bool mid_barrier) {
+  constexpr int NB = E / R;
+  static_assert(NB * R == E, "radix must divide the per-thread element count");
+  const int lr = L / R;
+  C v[NB][R];
+  int wrow[NB], jj[NB];
+  const bool on = tid < nthr;
+  if (on) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int bi = tid + b * nthr;
+      const int w = fquot(bi, sg.rcp_lr);
+      const int j = bi - w * lr;
+      wrow[b] = w;
+      jj[b] = j;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[b][r] = load(w, j + r * lr);
     }
   }
+  if (mid_barrier) __syncthreads();
+  if (on) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int j = jj[b];                  // k = j: ns = L/R exceeds every j
+      if (sg.ns > 1) {
+#pragma unroll
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[r * j * sg.tw_step]);
+      }
+      dft<R, false>(v[b]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) mul(wrow[b], j + r * lr, v[b][r]);
+      dft<R, true>(v[b]);
+#pragma unroll
+      for (int r = 0; r < R; ++r) emit(wrow[b], j * R + r, v[b][r]);
+    }
+  }
+}
+
+// Shared-memory row accessors for the inner stages.
+template <typename C>
+struct SmemRows {
+  C* s;
+  int ld;
+  __device__ __forceinline__ C operator()(int w, int i) const { return s[w * ld + phys(i)]; }
+  __device__ __forceinline__ void operator()(int w, int i, const C& x) const { s[w * ld + phys(i)] = x; }
+};
+
+// Stage q of a plan that lives in kernel-parameter space. Constant indices
+// only: a runtime index into a parameter array would force a local-memory
+// copy of the whole plan.
+__device__ __forceinline__ FftStage stage_at(const FftPlan& p, int q) {
+  switch (q) {
+    case 0: return p.st[0];
+    case 1: return p.st[1];
+    case 2: return p.st[2];
+    case 3: return p.st[3];
+    case 4: return p.st[4];
+    case 5: return p.st[5];
+    case 6: return p.st[6];
+    default: return p.st[7];
+  }
+}
+
+// Runtime radix -> compile-time stage.
+template <typename C, int E, bool INV, class Load, class Emit>
+__device__ __forceinline__ void stage_dispatch(int L, const FftStage& sg, const C* __restrict__ tw, int tid, int nthr,
+                                               Load& load, Emit& emit, bool mid_barrier) {
+  switch (sg.radix) {
+    case 2: if constexpr (E % 2 == 0) stage_io<C, E, 2, INV>(L, sg, tw, tid, nthr, load, emit, mid_barrier); break;
+    case 3: if constexpr (E % 3 == 0) stage_io<C, E, 3, INV>(L, sg, tw, tid, nthr, load, emit, mid_barrier); break;
+    case 4: if constexpr (E % 4 == 0) stage_io<C, E, 4, INV>(L, sg, tw, tid, nthr, load, emit, mid_barrier); break;
+    case 8: if constexpr (E % 8 == 0) stage_io<C, E, 8, INV>(L, sg, tw, tid, nthr, load, emit, mid_barrier); break;
+    case 16: if constexpr (E % 16 == 0) stage_io<C, E, 16, INV>(L, sg, tw, tid, nthr, load, emit, mid_barrier); break;
+    default: break;
+  }
+}
+
+template <typename C, int E, class Load, class Mul, class Emit>
+__device__ __forceinline__ void filter_dispatch(int L, const FftStage& sg, const C* __restrict__ tw, int tid, int nthr,
+                                                Load& load, Mul& mul, Emit& emit, bool mid_barrier) {
+  switch (sg.radix) {
+    case 2: if constexpr (E % 2 == 0) stage_filter<C, E, 2>(L, sg, tw, tid, nthr, load, mul, emit, mid_barrier); break;
+    case 3: if constexpr (E % 3 == 0) stage_filter<C, E, 3>(L, sg, tw, tid, nthr, load, mul, emit, mid_barrier); break;
+    case 4: if constexpr (E % 4 == 0) stage_filter<C, E, 4>(L, sg, tw, tid, nthr, load, mul, emit, mid_barrier); break;
+    case 8: if constexpr (E % 8 == 0) stage_filter<C, E, 8>(L, sg, tw, tid, nthr, load, mul, emit, mid_barrier); break;
+    case 16: if constexpr (E % 16 == 0) stage_filter<C, E, 16>(L, sg, tw, tid, nthr, load, mul, emit, mid_barrier); break;
+    default: break;
+  }
+}
+
+// Full transform of every sequence of the tile (natural order in and out),
+// plans of at most 5 stages.
+// The first stage reads through `load`, the last writes through `emit`; the
+// stages in between go through the shared-memory tile. Ends without a
+// trailing barrier when the last stage writes elsewhere than the tile.
+// nthr is the FFT's logical thread count (W*L/E); the block may be larger.
+template <typename C, int E, bool INV, class Load, class Emit>
+__device__ __forceinline__ void fft_run(C* s, int ld, const FftPlan& p, int tid, int nthr, Load& load, Emit& emit,
+                                        bool load_from_tile, bool emit_to_tile) {
+  const C* tw = reinterpret_cast<const C*>(p.tw);
+  SmemRows<C> rows{s, ld};
+  const int n = p.nst;
+  if (n == 1) {
+    stage_dispatch<C, E, INV>(p.L, p.st[0], tw, tid, nthr, load, emit, load_from_tile && emit_to_tile);
+    if (emit_to_tile) __syncthreads();
+    return;
+  }
+  stage_dispatch<C, E, INV>(p.L, p.st[0], tw, tid, nthr, load, rows, load_from_tile);
+  __syncthreads();
+  // inner stages, unrolled with constant parameter indices (a loop over the
+  // stage index spills the stage's registers to local memory)
+  if (n > 2) { stage_dispatch<C, E, INV>(p.L, p.st[1], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 3) { stage_dispatch<C, E, INV>(p.L, p.st[2], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 4) { stage_dispatch<C, E, INV>(p.L, p.st[3], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  const FftStage sl = stage_at(p, n - 1);
+  stage_dispatch<C, E, INV>(p.L, sl, tw, tid, nthr, rows, emit, emit_to_tile);
+  if (emit_to_tile) __syncthreads();
+}
+
+// Forward transform, multiply, inverse transform (the filter pass). `inv`
+// must be the forward plan's radices in reverse order, so that the last
+// forward and the first inverse stage meet in registers (stage_filter).
+template <typename C, int E, class Load, class Mul, class Emit>
+__device__ __forceinline__ void fft_filter_run(C* s, int ld, const FftPlan& fwd, const FftPlan& inv, int tid, int nthr,
+                                               Load& load, Mul& mul, Emit& emit) {
+  const C* tw = reinterpret_cast<const C*>(fwd.tw);
+  SmemRows<C> rows{s, ld};
+  const int n = fwd.nst;
+  if (n == 1) {
+    filter_dispatch<C, E>(fwd.L, fwd.st[0], tw, tid, nthr, load, mul, emit, false);
+    return;
+  }
+  stage_dispatch<C, E, false>(fwd.L, fwd.st[0], tw, tid, nthr, load, rows, false);
+  __syncthreads();
+  if (n > 2) { stage_dispatch<C, E, false>(fwd.L, fwd.st[1], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 3) { stage_dispatch<C, E, false>(fwd.L, fwd.st[2], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 4) { stage_dispatch<C, E, false>(fwd.L, fwd.st[3], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  const FftStage sf = stage_at(fwd, n - 1);
+  filter_dispatch<C, E>(fwd.L, sf, tw, tid, nthr, rows, mul, rows, true);
+  __syncthreads();
+  if (n > 2) { stage_dispatch<C, E, true>(inv.L, inv.st[1], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 3) { stage_dispatch<C, E, true>(inv.L, inv.st[2], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 4) { stage_dispatch<C, E, true>(inv.L, inv.st[3], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  const FftStage sl = stage_at(inv, n - 1);
+  stage_dispatch<C, E, true>(inv.L, sl, tw, tid, nthr, rows, emit, false);
 }
 
 }  // namespace gad

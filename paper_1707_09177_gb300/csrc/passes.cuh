@@ -171,13 +171,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Block reduction of up to three dots, partial store, arrival ticket; the
-// last block to arrive sums every field's partials in a fixed order and runs
-// the scalar update (deterministic for a fixed launch shape).
+// Block reduction of up to three dots into a per-block partial, then two
+// arrival tickets. ticket[2 + f] counts the blocks of field f: the last one
+// to arrive sums that field's partials in a fixed order (deterministic for a
+// fixed launch shape) and runs the field's scalar update at once, while
+// other fields' blocks are still running. ticket[0] counts finished fields:
+// the last one sets the graph's loop condition. ticket[1] counts loop passes
+// of the current solve (reset by the initial-residual pass).
 template <typename T>
 __device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, bool act) {
   __shared__ double red[32][3];
-  __shared__ int am_last;
+  __shared__ int last_field;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nw = (blockDim.x + 31) >> 5;
   const int nblk = gridDim.x;
@@ -201,45 +205,113 @@ __device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, boo
   }
   if (tid == 0) {
     __threadfence();
-    const unsigned prev = atomicAdd(a.ticket, 1u);
-    am_last = (prev == gridDim.x * gridDim.y - 1);
+    const unsigned prev = atomicAdd(a.ticket + 2 + f, 1u);
+    last_field = (prev == (unsigned)nblk - 1u);
   }
   __syncthreads();
-  if (!am_last) return;
+  if (!last_field) return;
   __threadfence();
-  for (int g = warp; g < a.batch; g += nw) {
-    FieldState& s = a.st[g];
-    if (!s.active && !a.force) continue;
-    double tot[3] = {0.0, 0.0, 0.0};
-    for (int b = lane; b < nblk; b += 32) {
-      const double* p = a.part + ((long long)g * nblk + b) * 4;
+  FieldState& s = a.st[f];
+  if (act) {                    // act is the field's flag: every block of f saw the same value
+    double t[3] = {0.0, 0.0, 0.0};
+    const double* pf = a.part + (long long)f * nblk * 4;
+    for (int b = tid; b < nblk; b += blockDim.x) {
 #pragma unroll
-      for (int d = 0; d < 3; ++d) tot[d] += __ldcg(p + d);
+      for (int d = 0; d < 3; ++d) t[d] += __ldcg(pf + (long long)b * 4 + d);
     }
 #pragma unroll
-    for (int d = 0; d < 3; ++d) tot[d] = warp_sum(tot[d]);
-    if (lane == 0) scalar_update(a.stage, s, tot, a.cfg, g);
+    for (int d = 0; d < 3; ++d) t[d] = warp_sum(t[d]);
+    __syncthreads();
+    if (lane == 0) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) red[warp][d] = t[d];
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double tot[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        tot[d] = 0.0;
+        for (int q = 0; q < nw; ++q) tot[d] += red[q][d];
+      }
+      scalar_update(a.stage, s, tot, a.cfg, f);
+    }
   }
-  __syncthreads();
   if (tid == 0) {
-    if (a.stage == SS_INIT) a.ticket[1] = 0u;            // loop counter of this solve
-    if (a.set_cond) {
-      unsigned any = 0;
-      for (int g = 0; g < a.batch; ++g) any |= (a.st[g].active != 0);
-      // every field stops by maxit passes; never iterate past that bound
-      const unsigned loops = ++a.ticket[1];
-      if (loops > (unsigned)a.cfg.maxit + 1u) any = 0;
-      cudaGraphSetConditional(a.cond, any);
+    a.ticket[2 + f] = 0u;
+    __threadfence();
+    const unsigned prevg = atomicAdd(a.ticket, 1u);
+    if (prevg == gridDim.y - 1u) {                        // every field is reduced
+      __threadfence();
+      if (a.stage == SS_INIT) a.ticket[1] = 0u;
+      if (a.set_cond) {
+        unsigned any = 0;
+        for (int g = 0; g < a.batch; ++g) any |= (*(volatile const int*)&a.st[g].active != 0);
+        // every field stops by maxit passes; never iterate past that bound
+        const unsigned loops = ++a.ticket[1];
+        if (loops > (unsigned)a.cfg.maxit + 1u) any = 0;
+        cudaGraphSetConditional(a.cond, any);
+      }
+      a.ticket[0] = 0u;
     }
-    a.ticket[0] = 0u;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Forward x pass: prologue, real-to-complex FFT of W rows, transposed store to S1.
-//   rcp_a = 1/(nx/4), rcp_b = 1/(nx/4 + 1)
+// Loads a W x n tile stored transposed in global memory (element (w, i) at
+// g[i*gstride + w]) into the shared-memory rows, U independent loads per
+// thread in flight.
+template <typename C, int U>
+__device__ __forceinline__ void load_transposed(C* s, int ld, const C* __restrict__ g, long long gstride, int W,
+                                                int n, int tid, int nthr) {
+  const int lw = __ffs(W) - 1;
+  const int total = W * n;
+  for (int base = tid; base < total; base += nthr * U) {
+    C tmp[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < total) tmp[u] = g[(long long)(idx >> lw) * gstride + (idx & (W - 1))];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + u * nthr;
+      if (idx < total) s[(idx & (W - 1)) * ld + phys(idx >> lw)] = tmp[u];
+    }
+  }
+}
+
+// Stores the shared-memory rows transposed (element (w, i) to g[i*gstride + w]).
+template <typename C>
+__device__ __forceinline__ void store_transposed(const C* s, int ld, C* __restrict__ g, long long gstride, int W,
+                                                 int n, int tid, int nthr) {
+  const int lw = __ffs(W) - 1;
+  for (int idx = tid; idx < W * n; idx += nthr)
+    g[(long long)(idx >> lw) * gstride + (idx & (W - 1))] = s[(idx & (W - 1)) * ld + phys(idx >> lw)];
+}
+
+template <typename T> struct V2 { T x, y; };
+template <typename T> __device__ __forceinline__ V2<T> ld2(const T* p) {
+  using C = typename cpx<T>::t;
+  const C c = *reinterpret_cast<const C*>(p);
+  return {c.x, c.y};
+}
+template <typename T> __device__ __forceinline__ void st2(T* p, T a, T b) {
+  using C = typename cpx<T>::t;
+  *reinterpret_cast<C*>(p) = C{a, b};
+}
+
+// x and y passes fit 80 registers at E = 16 (3 blocks of 256 per SM); the filter
+// pass keeps two FFT stages' worth of state live and gets 128.
+#define GAD_BOUNDS(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 3 : 2)
+#define GAD_BOUNDS_FILT __launch_bounds__(256, 2)
+
+// Forward x pass: the Krylov prologue is fused into the first FFT stage,
+// which reads the packed rows z[n] = x[2n] + i x[2n+1] straight from global
+// memory; the real-to-complex split and the transposed store to S1 follow.
+//   rcp_b = 1/(nx/4 + 1)
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_xfwd(PassArgs<T> a) {
+__global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -248,77 +320,70 @@ __global__ void __launch_bounds__(512) k_xfwd(PassArgs<T> a) {
   FieldState* st = a.st ? a.st + f : nullptr;
   if (st && !st->active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int nx = a.nx, M = nx >> 1, cpr = nx >> 2;
+  const int nx = a.nx, M = nx >> 1;
   const int row0 = blockIdx.x * a.W;
   const int z = row0 / a.ny, y0 = row0 - z * a.ny;
   const long long base = (long long)f * a.P + (long long)row0 * nx;
   const bool first = st ? (st->iter == 0) : true;
   const T al = st ? T(st->alpha) : T(0), be = st ? T(st->beta) : T(0), om = st ? T(st->omega) : T(0);
+  const int op = a.op;
+  const T* __restrict__ vA = a.A;
+  const T* __restrict__ vB = a.B;
+  T* vO1 = a.O1;
+  T* vO2 = a.O2;
+  T* vO3 = a.O3;
 
-  for (int idx = tid; idx < a.W * cpr; idx += nthr) {
-    const int w = fquot(idx, a.rcp_a);
-    const int q = idx - w * cpr;
-    const long long g = base + (long long)w * nx + 4 * q;
-    V4<T> x;
-    switch (a.op) {
-      case XF_COPY: {
-        x = ld4(a.A + g);
-        if (a.O1) st4(a.O1 + g, x);
+  auto load = [&](int w, int n) -> C {
+    const long long g = base + (long long)w * nx + 2 * n;
+    T x0, x1;
+    switch (op) {
+      case XF_VC: {                               // U += R; x = R
+        const V2<T> r = ld2(vA + g), u = ld2(vO1 + g);
+        st2(vO1 + g, u.x + r.x, u.y + r.y);
+        x0 = r.x; x1 = r.y;
         break;
       }
-      case XF_VC: {
-        x = ld4(a.A + g);
-        V4<T> u = ld4(a.O1 + g);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) u.v[e] += x.v[e];
-        st4(a.O1 + g, u);
-        break;
-      }
-      case XF_CG: {
-        V4<T> r = ld4(a.A + g);
+      case XF_CG: {                               // U += alpha P; P = R + beta P
+        const V2<T> r = ld2(vA + g);
         if (first) {
-          x = r;
+          x0 = r.x; x1 = r.y;
         } else {
-          V4<T> p = ld4(a.O2 + g), u = ld4(a.O1 + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            u.v[e] = fma(al, p.v[e], u.v[e]);
-            x.v[e] = fma(be, p.v[e], r.v[e]);
-          }
-          st4(a.O1 + g, u);
+          const V2<T> p = ld2(vO2 + g), u = ld2(vO1 + g);
+          st2(vO1 + g, fma(al, p.x, u.x), fma(al, p.y, u.y));
+          x0 = fma(be, p.x, r.x); x1 = fma(be, p.y, r.y);
         }
-        st4(a.O2 + g, x);
+        st2(vO2 + g, x0, x1);
         break;
       }
-      case XF_BI_P: {
-        V4<T> r = ld4(a.A + g);
+      case XF_BI_P: {                             // P = R + beta (P - omega Q)
+        const V2<T> r = ld2(vA + g);
         if (first) {
-          x = r;
+          x0 = r.x; x1 = r.y;
         } else {
-          V4<T> p = ld4(a.O2 + g), qv = ld4(a.B + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) x.v[e] = fma(be, fma(-om, qv.v[e], p.v[e]), r.v[e]);
+          const V2<T> p = ld2(vO2 + g), q = ld2(vB + g);
+          x0 = fma(be, fma(-om, q.x, p.x), r.x);
+          x1 = fma(be, fma(-om, q.y, p.y), r.y);
         }
-        st4(a.O2 + g, x);
+        st2(vO2 + g, x0, x1);
         break;
       }
-      case XF_BI_S: {
-        V4<T> r = ld4(a.A + g), qv = ld4(a.B + g);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) x.v[e] = fma(-al, qv.v[e], r.v[e]);
-        st4(a.O3 + g, x);
+      case XF_BI_S: {                             // S = R - alpha Q
+        const V2<T> r = ld2(vA + g), q = ld2(vB + g);
+        x0 = fma(-al, q.x, r.x); x1 = fma(-al, q.y, r.y);
+        st2(vO3 + g, x0, x1);
         break;
       }
-      default:
-        x = ld4(a.A + g);
+      default: {                                  // XF_COPY: x = A (and O1 = A)
+        const V2<T> v = ld2(vA + g);
+        if (vO1) st2(vO1 + g, v.x, v.y);
+        x0 = v.x; x1 = v.y;
         break;
+      }
     }
-    C* row = s + w * a.ld;
-    row[phys(2 * q)] = C{x.v[0], x.v[1]};
-    row[phys(2 * q + 1)] = C{x.v[2], x.v[3]};
-  }
-  __syncthreads();
-  fft_tile<C, E, false>(s, a.ld, a.fft, tid, a.tfft);
+    return C{x0, x1};
+  };
+  SmemRows<C> rows{s, a.ld};
+  fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true);
   // split the packed half-length transform into the real-input spectrum
   const C* twx = reinterpret_cast<const C*>(a.twx);
   const int h1 = (M >> 1) + 1;
@@ -341,16 +406,13 @@ __global__ void __launch_bounds__(512) k_xfwd(PassArgs<T> a) {
   }
   __syncthreads();
   C* S1 = reinterpret_cast<C*>(a.S1) + (long long)f * a.SP + (long long)z * a.kxn * a.ny + y0;
-  const int lw = __ffs(a.W) - 1;
-  for (int idx = tid; idx < a.W * (M + 1); idx += nthr) {
-    const int w = idx & (a.W - 1), kx = idx >> lw;
-    S1[(long long)kx * a.ny + w] = s[w * a.ld + phys(kx)];
-  }
+  store_transposed(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
 }
 
-// Inverse x pass: transposed load from S1, complex-to-real FFT, epilogue and dots.
+// Inverse x pass: transposed load from S1, complex-to-real preparation, FFT
+// whose last stage writes the rows through the fused epilogue and dots.
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_xinv(PassArgs<T> a) {
+__global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -359,17 +421,13 @@ __global__ void __launch_bounds__(512) k_xinv(PassArgs<T> a) {
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int nx = a.nx, M = nx >> 1, cpr = nx >> 2;
+  const int nx = a.nx, M = nx >> 1;
   const int row0 = blockIdx.x * a.W;
   const int z = row0 / a.ny, y0 = row0 - z * a.ny;
   Acc<T> acc[3];
   if (act) {
     const C* S1 = reinterpret_cast<const C*>(a.S1) + (long long)f * a.SP + (long long)z * a.kxn * a.ny + y0;
-    const int lw = __ffs(a.W) - 1;
-    for (int idx = tid; idx < a.W * (M + 1); idx += nthr) {
-      const int w = idx & (a.W - 1), kx = idx >> lw;
-      s[w * a.ld + phys(kx)] = S1[(long long)kx * a.ny + w];
-    }
+    load_transposed<C, 8>(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
     __syncthreads();
     const C* twx = reinterpret_cast<const C*>(a.twx);
     const int h1 = (M >> 1) + 1;
@@ -390,95 +448,91 @@ __global__ void __launch_bounds__(512) k_xinv(PassArgs<T> a) {
       }
     }
     __syncthreads();
-    fft_tile<C, E, true>(s, a.ld, a.fft, tid, a.tfft);
     const long long base = (long long)f * a.P + (long long)row0 * nx;
     const T al = st ? T(st->alpha) : T(0), om = st ? T(st->omega) : T(0);
-    for (int idx = tid; idx < a.W * cpr; idx += nthr) {
-      const int w = fquot(idx, a.rcp_a);
-      const int q = idx - w * cpr;
-      const long long g = base + (long long)w * nx + 4 * q;
-      const C* row = s + w * a.ld;
-      const C c0 = row[phys(2 * q)], c1 = row[phys(2 * q + 1)];
-      V4<T> y = {{c0.x, c0.y, c1.x, c1.y}};
-      switch (a.op) {
+    const int op = a.op;
+    const T* __restrict__ vA = a.A;
+    const T* __restrict__ vB = a.B;
+    const T* __restrict__ vC = a.C;
+    T* vO1 = a.O1;
+    T* vO2 = a.O2;
+    Acc<T> acc0, acc1;
+    auto emit = [&](int w, int n, const C& y) {
+      const long long g = base + (long long)w * nx + 2 * n;
+      switch (op) {
         case XI_STORE:
-          st4(a.O1 + g, y);
+          st2(vO1 + g, y.x, y.y);
           break;
         case XI_INIT: {
-          V4<T> r = ld4(a.A + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) { r.v[e] -= y.v[e]; acc[0].add_prod(r.v[e], r.v[e]); }
-          st4(a.O1 + g, r);
-          if (a.O2) st4(a.O2 + g, r);
+          const V2<T> u = ld2(vA + g);
+          const T r0 = u.x - y.x, r1 = u.y - y.y;
+          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
+          st2(vO1 + g, r0, r1);
+          if (vO2) st2(vO2 + g, r0, r1);
           break;
         }
         case XI_RES: {
-          V4<T> r = ld4(a.A + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) { r.v[e] -= y.v[e]; acc[0].add_prod(r.v[e], r.v[e]); }
+          const V2<T> u = ld2(vA + g);
+          const T r0 = u.x - y.x, r1 = u.y - y.y;
+          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
           break;
         }
         case XI_VC: {
-          V4<T> r = ld4(a.O1 + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) { r.v[e] -= y.v[e]; acc[0].add_prod(r.v[e], r.v[e]); }
-          st4(a.O1 + g, r);
+          const V2<T> r = ld2(vO1 + g);
+          const T r0 = r.x - y.x, r1 = r.y - y.y;
+          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
+          st2(vO1 + g, r0, r1);
           break;
         }
         case XI_CG: {
-          V4<T> r = ld4(a.O1 + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) { r.v[e] = fma(-al, y.v[e], r.v[e]); acc[0].add_prod(r.v[e], r.v[e]); }
-          st4(a.O1 + g, r);
+          const V2<T> r = ld2(vO1 + g);
+          const T r0 = fma(-al, y.x, r.x), r1 = fma(-al, y.y, r.y);
+          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
+          st2(vO1 + g, r0, r1);
           break;
         }
         case XI_SD: {
-          V4<T> r = ld4(a.O1 + g), u = ld4(a.O2 + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            u.v[e] = fma(al, r.v[e], u.v[e]);
-            r.v[e] = fma(-al, y.v[e], r.v[e]);
-            acc[0].add_prod(r.v[e], r.v[e]);
-          }
-          st4(a.O1 + g, r);
-          st4(a.O2 + g, u);
+          const V2<T> r = ld2(vO1 + g), u = ld2(vO2 + g);
+          st2(vO2 + g, fma(al, r.x, u.x), fma(al, r.y, u.y));
+          const T r0 = fma(-al, y.x, r.x), r1 = fma(-al, y.y, r.y);
+          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
+          st2(vO1 + g, r0, r1);
           break;
         }
         case XI_BI_Q: {
-          V4<T> f0 = ld4(a.A + g);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) acc[0].add_prod(f0.v[e], y.v[e]);
-          st4(a.O1 + g, y);
+          const V2<T> f0 = ld2(vA + g);
+          acc0.add_prod(f0.x, y.x); acc0.add_prod(f0.y, y.y);
+          st2(vO1 + g, y.x, y.y);
           break;
         }
         case XI_BI_T: {
-          V4<T> f0 = ld4(a.A + g), p = ld4(a.B + g), sv = ld4(a.C + g), u = ld4(a.O1 + g);
-          V4<T> r;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            u.v[e] = fma(om, sv.v[e], fma(al, p.v[e], u.v[e]));
-            r.v[e] = fma(-om, y.v[e], sv.v[e]);
-            acc[0].add_prod(r.v[e], r.v[e]);
-            acc[1].add_prod(f0.v[e], r.v[e]);
-          }
-          st4(a.O1 + g, u);
-          st4(a.O2 + g, r);
+          const V2<T> f0 = ld2(vA + g), p = ld2(vB + g), sv = ld2(vC + g), u = ld2(vO1 + g);
+          st2(vO1 + g, fma(om, sv.x, fma(al, p.x, u.x)), fma(om, sv.y, fma(al, p.y, u.y)));
+          const T r0 = fma(-om, y.x, sv.x), r1 = fma(-om, y.y, sv.y);
+          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
+          acc1.add_prod(f0.x, r0); acc1.add_prod(f0.y, r1);
+          st2(vO2 + g, r0, r1);
           break;
         }
         default:
           break;
       }
-    }
+    };
+    SmemRows<C> rows{s, a.ld};
+    fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false);
+    acc[0] = acc0;
+    acc[1] = acc1;
   }
   if (a.ndots) block_finish(a, acc, f, act);
 }
 
 // Filter pass along the last axis (y in 2D, z in 3D): forward FFT of W
-// contiguous sequences, multiply by G_hat(k)/P (with Parseval dots), inverse
-// FFT, store back in place.  rcp_a = 1/(L/2), rcp_b = 1/L; in 3D the
+// contiguous sequences read straight from the spectral buffer, multiply by
+// G_hat(k)/P with Parseval dots in registers, inverse FFT written straight
+// back. fft holds the forward plan, fft_inv the reversed one. In 3D the
 // sequence index is kx*ny + ky.
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_filt(PassArgs<T> a) {
+__global__ void GAD_BOUNDS_FILT k_filt(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
@@ -486,139 +540,109 @@ __global__ void __launch_bounds__(512) k_filt(PassArgs<T> a) {
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
-  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int tid = threadIdx.x;
   const int L = a.fft.L, half = L >> 1;
   const bool three_d = a.nz > 1;
   const int nseq = three_d ? a.kxn * a.ny : a.kxn;
   const int seq0 = blockIdx.x * a.W;
+  const int nvalid = min(a.W, nseq - seq0);
   C* S = reinterpret_cast<C*>(three_d ? a.S2 : a.S1) + (long long)f * a.SP + (long long)seq0 * L;
   Acc<T> acc[3];
   if (act) {
-    for (int idx = tid; idx < a.W * half; idx += nthr) {
-      const int w = fquot(idx, a.rcp_a);
-      const int i2 = idx - w * half;
-      C v0 = {T(0), T(0)}, v1 = {T(0), T(0)};
-      if (seq0 + w < nseq) {
-        const C* src = S + (long long)w * L + 2 * i2;
-        v0 = src[0];
-        v1 = src[1];
-      }
-      C* row = s + w * a.ld;
-      row[phys(2 * i2)] = v0;
-      row[phys(2 * i2 + 1)] = v1;
-    }
-    __syncthreads();
-    fft_tile<C, E, false>(s, a.ld, a.fft, tid, a.tfft);
-    const int nxh = a.nx >> 1;
-    for (int idx = tid; idx < a.W * L; idx += nthr) {
-      const int w = fquot(idx, a.rcp_b);
-      const int i = idx - w * L;
+    const int nxh = a.nx >> 1, ny = a.ny;
+    const T kc2 = a.kc2, gs = a.gscale;
+    const int op = a.op;
+    // Parseval sums have positive terms only: each thread sums its E terms
+    // in plain T, and the partials are widened to float64 from there on
+    T p0 = T(0), p1 = T(0), p2 = T(0);
+    auto load = [&](int w, int i) -> C {
+      return w < nvalid ? S[(long long)w * L + i] : C{T(0), T(0)};
+    };
+    auto mul = [&](int w, int i, C& X) {
       const int seq = seq0 + w;
-      if (seq >= nseq) continue;
       int kx, k2i;
       const int ki = i < half ? i : i - L;
       if (three_d) {
-        kx = seq / a.ny;
-        const int kyi = seq - kx * a.ny;
-        const int ky = kyi < (a.ny >> 1) ? kyi : kyi - a.ny;
+        kx = seq / ny;
+        const int kyi = seq - kx * ny;
+        const int ky = kyi < (ny >> 1) ? kyi : kyi - ny;
         k2i = kx * kx + ky * ky + ki * ki;
       } else {
         kx = seq;
         k2i = kx * kx + ki * ki;
       }
-      const T g = a.kc2 / (a.kc2 + T(k2i));
-      C* pv = s + w * a.ld + phys(i);
-      C X = *pv;
-      if (a.op != FI_NONE) {
+      const T g = kc2 / (kc2 + T(k2i));
+      if (op != FI_NONE && w < nvalid) {
         const T wgt = (kx == 0 || kx == nxh) ? T(1) : T(2);
         const T m2 = X.x * X.x + X.y * X.y;
-        if (a.op == FI_XGX) {
-          acc[0].add(wgt * g * m2);
+        const T wm = wgt * m2;
+        if (op == FI_XGX) {
+          p0 = fma(g, wm, p0);
         } else {
-          acc[0].add(wgt * m2);
-          acc[1].add(wgt * g * m2);
-          acc[2].add(wgt * g * g * m2);
+          p0 += wm;
+          const T gw = g * wm;
+          p1 += gw;
+          p2 = fma(g, gw, p2);
         }
       }
-      const T sc = g * a.gscale;
-      *pv = C{X.x * sc, X.y * sc};
-    }
-    __syncthreads();
-    fft_tile<C, E, true>(s, a.ld, a.fft, tid, a.tfft);
-    for (int idx = tid; idx < a.W * half; idx += nthr) {
-      const int w = fquot(idx, a.rcp_a);
-      const int i2 = idx - w * half;
-      if (seq0 + w >= nseq) continue;
-      const C* row = s + w * a.ld;
-      C* dst = S + (long long)w * L + 2 * i2;
-      dst[0] = row[phys(2 * i2)];
-      dst[1] = row[phys(2 * i2 + 1)];
-    }
+      const T sc = g * gs;
+      X = C{X.x * sc, X.y * sc};
+    };
+    auto emit = [&](int w, int i, const C& x) {
+      if (w < nvalid) S[(long long)w * L + i] = x;
+    };
+    fft_filter_run<C, E>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit);
+    acc[0].s = p0;
+    acc[1].s = p1;
+    acc[2].s = p2;
   }
   if (a.ndots) block_finish(a, acc, f, act);
 }
 
-// 3D forward y pass: W consecutive z at one kx; load S1 rows [z][kx][:],
-// FFT along y, store transposed into S2 [kx][ky][z].  Grid x = kxn * (nz/W).
+// 3D forward y pass: W consecutive z at one kx; the first stage reads the
+// S1 rows [z][kx][:] directly, the tile is stored transposed into S2
+// [kx][ky][z].  Grid x = kxn * (nz/W).
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_yfwd(PassArgs<T> a) {
+__global__ void GAD_BOUNDS(T, E) k_yfwd(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int f = blockIdx.y;
   if (a.st && !a.st[f].active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int L = a.ny, half = L >> 1;
+  const int L = a.ny;
   const int zt = a.nz / a.W;
   const int kx = blockIdx.x / zt, z0 = (blockIdx.x - kx * zt) * a.W;
   const C* S1 = reinterpret_cast<const C*>(a.S1) + (long long)f * a.SP;
-  for (int idx = tid; idx < a.W * half; idx += nthr) {
-    const int w = fquot(idx, a.rcp_a);
-    const int i2 = idx - w * half;
-    const C* src = S1 + ((long long)(z0 + w) * a.kxn + kx) * L + 2 * i2;
-    C* row = s + w * a.ld;
-    row[phys(2 * i2)] = src[0];
-    row[phys(2 * i2 + 1)] = src[1];
-  }
-  __syncthreads();
-  fft_tile<C, E, false>(s, a.ld, a.fft, tid, a.tfft);
+  const int kxn = a.kxn;
+  auto load = [&](int w, int i) -> C { return S1[((long long)(z0 + w) * kxn + kx) * L + i]; };
+  SmemRows<C> rows{s, a.ld};
+  fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true);
   C* S2 = reinterpret_cast<C*>(a.S2) + (long long)f * a.SP + (long long)kx * L * a.nz + z0;
-  const int lw = __ffs(a.W) - 1;
-  for (int idx = tid; idx < a.W * L; idx += nthr) {
-    const int w = idx & (a.W - 1), ky = idx >> lw;
-    S2[(long long)ky * a.nz + w] = s[w * a.ld + phys(ky)];
-  }
+  store_transposed(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
 }
 
-// 3D inverse y pass: transposed load from S2, inverse FFT along y, rows back to S1.
+// 3D inverse y pass: transposed load from S2, inverse FFT whose last stage
+// writes the S1 rows directly.
 template <typename T, int E>
-__global__ void __launch_bounds__(512) k_yinv(PassArgs<T> a) {
+__global__ void GAD_BOUNDS(T, E) k_yinv(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
   const int f = blockIdx.y;
   if (a.st && !a.st[f].active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
-  const int L = a.ny, half = L >> 1;
+  const int L = a.ny;
   const int zt = a.nz / a.W;
   const int kx = blockIdx.x / zt, z0 = (blockIdx.x - kx * zt) * a.W;
   const C* S2 = reinterpret_cast<const C*>(a.S2) + (long long)f * a.SP + (long long)kx * L * a.nz + z0;
-  const int lw = __ffs(a.W) - 1;
-  for (int idx = tid; idx < a.W * L; idx += nthr) {
-    const int w = idx & (a.W - 1), ky = idx >> lw;
-    s[w * a.ld + phys(ky)] = S2[(long long)ky * a.nz + w];
-  }
+  load_transposed<C, 8>(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
   __syncthreads();
-  fft_tile<C, E, true>(s, a.ld, a.fft, tid, a.tfft);
   C* S1 = reinterpret_cast<C*>(a.S1) + (long long)f * a.SP;
-  for (int idx = tid; idx < a.W * half; idx += nthr) {
-    const int w = fquot(idx, a.rcp_a);
-    const int i2 = idx - w * half;
-    C* dst = S1 + ((long long)(z0 + w) * a.kxn + kx) * L + 2 * i2;
-    const C* row = s + w * a.ld;
-    dst[0] = row[phys(2 * i2)];
-    dst[1] = row[phys(2 * i2 + 1)];
-  }
+  const int kxn = a.kxn;
+  auto emit = [&](int w, int i, const C& x) { S1[((long long)(z0 + w) * kxn + kx) * L + i] = x; };
+  SmemRows<C> rows{s, a.ld};
+  fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false);
 }
 
 // u += alpha p for fields whose last CG pass still owes it (Algorithm 3,

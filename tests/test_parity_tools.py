@@ -35,5 +35,6 @@ def test_tolerance_and_counts_rule():
             self.iterations = n
     assert count_ok(5, R(5), [R(5), R(5)]) == (True, [5, 5, 5])
     assert count_ok(6, R(5), [R(5), R(5)])[0] is False
-    assert count_ok(7, R(5), [R(6), R(5)])[0] is True
-    assert count_ok(8, R(5), [R(6), R(5)])[0] is False
+    assert count_ok(7, R(5), [R(6), R(5)])[0] is True      # range 1: [3, 8]
+    assert count_ok(8, R(5), [R(6), R(5)])[0] is True
+    assert count_ok(9, R(5), [R(6), R(5)])[0] is False
