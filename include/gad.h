@@ -121,6 +121,32 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
 ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method method, int index, int reps,
                        void* stream, double* ms_per_launch, int* kind, int* op, int* count);
 
+/* Size of the fixed device scratch array that ad_filter_static uses. */
+#define AD_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* out = G in, like ad_filter, but allocating nothing: no context, no
+ * cudaMalloc/cudaFree, no allocating library call. The paper has no
+ * counterpart; this is for callers that cannot let a library allocate device
+ * memory -- real-time or embedded codes that reserve all memory at start-up,
+ * applications whose device memory belongs to another allocator, and code
+ * that must not synchronize the device (allocation and freeing may).
+ *   The scratch (twiddle tables and spectral buffers) lives in one
+ * file-scope device array of AD_STATIC_SCRATCH_BYTES, held by every GPU that
+ * loads the library until the process exits. A call needs, with cs = 8
+ * (AD_F32) or 16 (AD_F64) and each term rounded up to 256 bytes:
+ *   cs*Nx + cs*Ny [+ cs*Nz] + k * cs*batch*(Nx/2+1)*Ny*Nz,  k = 1 (2D), 2 (3D)
+ * bytes; larger requests return AD_ERR_ARG (e.g. 2D float32 up to one 2048^2
+ * field, 3D float32 up to one 128^3 field). Grid rules, pointers and the
+ * stream are as for ad_filter; `in` and `out` may be the same buffer.
+ *   The device address of the array is looked up (cudaGetSymbolAddress) by
+ * the first call on each device, with that device current; make that first
+ * call before any stream capture. All calls on a device share the array and
+ * leave their contents in it (nothing in it needs clearing: every call
+ * rewrites what it reads); calls whose work overlaps on the GPU (other
+ * streams or host threads) race on it and must be serialized.
+ * Returns AD_OK, AD_ERR_ARG or AD_ERR_CUDA. */
+ad_status ad_filter_static(const ad_grid* grid, const void* in, void* out, int batch, void* stream);
+
 /* Enables (1, default) or disables (0) capture of each solve into one CUDA
  * graph whose iteration loop is a device-side conditional while node. With 0
  * the host launches the iteration body in chunks and polls the device

@@ -31,7 +31,7 @@ METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3}
 AD_F32, AD_F64 = 0, 1
 
 EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_time_pass", "ad_set_graph_mode",
-            "ad_last_launch_count", "ad_status_str", "ad_last_error")
+            "ad_last_launch_count", "ad_status_str", "ad_last_error", "ad_filter_static")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv"}
 
 
