@@ -126,8 +126,12 @@ def test_f32_to_tolerance_counts(gad, method, shape, gamma):
     assert res.history[0, n_gpu] <= tol
     # the recurrence residual tracks the true one to float32 accuracy
     assert res.true_residual[0] < 20 * tol
-    ref64 = oracle.solve(method, ub.astype(np.float64), gamma, tol=tol, maxit=2000)
-    assert _rel(res.u.double().cpu().numpy(), ref64.u) < 1e-3
+    # against the exact (Fourier) inverse: ||u - u_ex|| <= ||r_true|| / G_hat_min
+    uex = oracle.exact_inverse(ub.astype(np.float64), gamma)
+    ref = np.linalg.norm(ub.astype(np.float64) - oracle.filter_field(ub.astype(np.float64), gamma))
+    gmin = oracle.transfer_function(shape, gamma).min()
+    err = np.linalg.norm(res.u.double().cpu().numpy() - uex)
+    assert err <= 1.05 * res.true_residual[0] * ref / gmin
 
 
 def test_edge_cases_per_field_status(gad):
