@@ -106,6 +106,37 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
                         const void* u0, int* iterations, ad_status* status,
                         double* res_hist, double* true_res, void* stream);
 
+/* Solves G u = u_bar for `nfields` fields of possibly different grids (2D and
+ * 3D, any supported sizes, dtypes and gammas) in one call: one CUDA graph
+ * whose concurrent branches each solve the fields of one grid shape (gathered
+ * into a contiguous workspace, solved with their own device-side while loop,
+ * scattered back). Same algorithms, stopping rules and precision as
+ * ad_deconvolve, u0 = u_bar for every field.
+ *   grids      host ad_grid[nfields]
+ *   ubar       host array of nfields device pointers (inputs)
+ *   u_out      host array of nfields device pointers (outputs, no aliasing)
+ *   iterations host int[nfields] (may be NULL)
+ *   status     host ad_status[nfields] (may be NULL)
+ *   res_hist   host array of nfields host pointers to double[maxit+1] (the
+ *              array or any entry may be NULL)
+ * The graph is built on the first call for a given set of grids, pointers,
+ * method, tol and maxit and reused afterwards. Returns AD_OK if every field
+ * converged, else the status of the first field (in group order) that did not.
+ * Batching of the paper's per-field solves; no counterpart in the paper. */
+ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, const void* const* ubar,
+                                void* const* u_out, ad_method method, double tol, int maxit, int* iterations,
+                                ad_status* status, double* const* res_hist, void* stream);
+
+/* Tile autotuner. With `grid` non-NULL, tunes the plan for (grid, batch):
+ * for every pass of one iteration of `method` it times each admissible tile
+ * width (32-256 threads per block, <= 100 KB shared memory) with CUDA events
+ * on the context's internal buffers and keeps the fastest; later solves on
+ * that plan use the tuned tiles (cached graphs are rebuilt). Blocks the host
+ * while timing. `enable_for_batched` != 0 makes ad_deconvolve_batched tune
+ * every plan it creates (0 turns that off); `grid` may be NULL to set only
+ * this flag. No counterpart in the paper. */
+ad_status ad_autotune(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method method, int enable_for_batched);
+
 /* Measures one pass kernel of an iteration of `method` for this grid and
  * batch: the kernel is launched once to warm up, then `reps` times back to
  * back on `stream` between two CUDA events, in exactly the launch shape and

@@ -30,8 +30,9 @@ AD_ERR_ARG, AD_ERR_NONFINITE, AD_ERR_CUDA, AD_ERR_TIMEOUT, AD_ERR_NOMEM = -1, -2
 METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3}
 AD_F32, AD_F64 = 0, 1
 
-EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_time_pass", "ad_set_graph_mode",
-            "ad_last_launch_count", "ad_status_str", "ad_last_error", "ad_filter_static")
+EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvolve_batched", "ad_time_pass",
+            "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
+            "ad_filter_static")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv"}
 
 
@@ -75,6 +76,11 @@ def load(path=None):
     lib.ad_deconvolve.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_i, c_d, c_i, c_p,
                                   c_p, c_p, c_p, c_p, c_p]
     lib.ad_deconvolve.restype = c_i
+    lib.ad_deconvolve_batched.argtypes = [c_p, c_i, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_d, c_i, c_p, c_p,
+                                          c_p, c_p]
+    lib.ad_deconvolve_batched.restype = c_i
+    lib.ad_autotune.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_i]
+    lib.ad_autotune.restype = c_i
     lib.ad_time_pass.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_i, c_i, c_p, c_p, c_p, c_p, c_p]
     lib.ad_time_pass.restype = c_i
     lib.ad_set_graph_mode.argtypes = [c_p, c_i]
@@ -231,3 +237,56 @@ def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, st
         _check(st, ctx)
         out.append(dict(index=i, kind=PASS_KINDS[kind.value], op=int(op.value), ms=float(ms.value)))
     return out
+
+
+def deconvolve_batched(fields, gammas, method="bicgstab", tol=1e-6, maxit=1000, ndims=None, outs=None,
+                       history=True, stream=None):
+    """Solves G u = u_bar for a list of fields of uneven size in one library
+    call (one CUDA graph). ``fields`` is a list of contiguous CUDA tensors,
+    each one field ((Ny, Nx) or (Nz, Ny, Nx)); ``gammas`` a list of filter
+    strengths. Returns (outputs, iterations, status, histories)."""
+    import torch
+    lib = load()
+    n = len(fields)
+    if n == 0:
+        return [], np.zeros(0, np.int32), np.zeros(0, np.int32), []
+    ctx = context(fields[0].device.index)
+    grids = (ad_grid * n)()
+    for i, (t, g) in enumerate(zip(fields, gammas)):
+        nd = (ndims[i] if ndims else t.dim())
+        gi, b, _ = _grid(t, nd, g)
+        if b != 1:
+            raise ValueError("deconvolve_batched takes one field per tensor")
+        grids[i] = gi
+    outs = outs if outs is not None else [torch.empty_like(t) for t in fields]
+    pin = (ctypes.c_void_p * n)(*[t.data_ptr() for t in fields])
+    pout = (ctypes.c_void_p * n)(*[t.data_ptr() for t in outs])
+    its = np.zeros(n, dtype=np.int32)
+    sts = np.zeros(n, dtype=np.int32)
+    hist = [np.full(int(maxit) + 1, np.nan) for _ in range(n)] if history else None
+    phist = (ctypes.c_void_p * n)(*[h.ctypes.data for h in hist]) if history else None
+    st = lib.ad_deconvolve_batched(ctx, n, grids, pin, pout, METHODS[method], float(tol), int(maxit),
+                                   ctypes.c_void_p(its.ctypes.data), ctypes.c_void_p(sts.ctypes.data),
+                                   phist, _stream_ptr(stream))
+    _check(st, ctx, per_field=True)
+    return outs, its, sts, hist
+
+
+def autotune(shape=None, gamma=0.1, batch=1, method="bicgstab", dtype="f32", for_batched=False, device=None):
+    """Tunes the tile widths of the plan for (shape, batch) by timing every
+    admissible width per pass (``shape=None``: only set whether batched solves
+    tune their plans)."""
+    lib = load()
+    ctx = context(device)
+    g = None
+    if shape is not None:
+        g = ad_grid()
+        g.ndim = len(shape)
+        rev = list(reversed(shape)) + [1] * (3 - len(shape))
+        for i in range(3):
+            g.n[i] = int(rev[i])
+        g.dtype = AD_F32 if dtype == "f32" else AD_F64
+        g.gamma = float(gamma)
+    st = lib.ad_autotune(ctx, ctypes.byref(g) if g is not None else None, int(batch), METHODS[method],
+                         1 if for_batched else 0)
+    _check(st, ctx)

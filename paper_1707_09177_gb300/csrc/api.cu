@@ -64,11 +64,14 @@ struct Plan {
   void *S1 = nullptr, *S2 = nullptr;
   void *R = nullptr, *Pv = nullptr, *Q = nullptr, *Sv = nullptr, *F0 = nullptr;
   void* Uscratch = nullptr;          // stands in for u when a single pass is timed
+  void *Bin = nullptr, *Bout = nullptr;   // batched solves: the group's fields gathered contiguously
   FieldState* st = nullptr;
   double* part = nullptr;
   unsigned* ticket = nullptr;
   double* hist = nullptr;
   int hist_cap = 0;
+  unsigned maxblk = 0;               // capacity of part (blocks per field)
+  bool tuned = false;
   std::vector<void*> owned;
 };
 
@@ -89,8 +92,24 @@ struct LaunchRec {
   PassArgs<double> ad{};
 };
 
+struct BatchedGroup {
+  Plan* p = nullptr;
+  std::vector<int> fields;          // indices into the caller's field arrays
+  int n_init = 0, n_body = 0, n_fin = 0;
+};
+
+struct BatchedEntry {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<BatchedGroup> groups;
+};
+
 struct ad_ctx {
+  bool autotune = false;                      // tune the tiles of every new plan of a batched solve
   std::vector<LaunchRec>* record = nullptr;   // when set, pass launches are recorded, not issued
+  std::map<std::string, BatchedEntry> bgraphs;
+  std::vector<cudaStream_t> branches;         // capture streams of the batched graph's branches
+  std::vector<cudaEvent_t> events;
   int device = 0;
   cudaStream_t cap = nullptr, cap2 = nullptr;
   bool use_graph = true;
@@ -332,7 +351,9 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
   const size_t vb = (size_t)p->P * batch * rs, sb = (size_t)p->SP * batch * cs;
   if ((s = dmalloc(ctx, p, &p->S1, sb)) != AD_OK ||
       (p->ndim == 3 && (s = dmalloc(ctx, p, &p->S2, sb)) != AD_OK)) { free_plan(p); return s; }
-  const unsigned maxblk = std::max(p->xi.grid.x, p->fl.grid.x);
+  // partials sized for the narrowest tile the autotuner may pick (1/8 of the default width)
+  const unsigned maxblk = 8 * std::max(p->xi.grid.x, p->fl.grid.x) + 8;
+  p->maxblk = maxblk;
   if ((s = dmalloc(ctx, p, (void**)&p->st, sizeof(FieldState) * batch)) != AD_OK ||
       (s = dmalloc(ctx, p, (void**)&p->part, sizeof(double) * 4 * maxblk * batch)) != AD_OK ||
       (s = dmalloc(ctx, p, (void**)&p->ticket, sizeof(unsigned) * (4 + batch))) != AD_OK) { free_plan(p); return s; }
@@ -363,6 +384,11 @@ void drop_graphs(ad_ctx* ctx) {
     if (kv.second.g) cudaGraphDestroy(kv.second.g);
   }
   ctx->graphs.clear();
+  for (auto& kv : ctx->bgraphs) {
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.g) cudaGraphDestroy(kv.second.g);
+  }
+  ctx->bgraphs.clear();
 }
 
 ad_status ensure_hist(ad_ctx* ctx, Plan* p, int maxit) {
@@ -663,6 +689,231 @@ ad_status run_solve(ad_ctx* ctx, Plan* p, const SolveIO& io, double tol, int max
   return AD_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Tile autotuner: for every pass of a plan, times each admissible tile width
+// (block sizes 32..256 threads, shared memory <= 100 KB, the partial-dot
+// capacity respected) in the launch configuration of one iteration of
+// `method`, on the plan's own buffers, and keeps the fastest.
+
+struct TileSlot {
+  PassCfg* pc;
+  int kind;
+  int L;
+  int slots;
+  int div;      // W must divide this (0: ragged tiles allowed)
+};
+
+void set_tile(const Plan* p, PassCfg& pc, int kind, int L, int slots, int W) {
+  int ld = phys_h(slots - 1) + 1;
+  if ((ld & 1) == 0) ++ld;
+  pc.W = W;
+  pc.T = (int)((long long)W * L / pc.E);
+  pc.ld = ld;
+  pc.smem = (size_t)W * ld * (p->f64 ? 16 : 8);
+  const int nseq = p->ndim == 3 ? p->kxn * p->ny : p->kxn;
+  switch (kind) {
+    case PK_XFWD: case PK_XINV: pc.grid = dim3(p->ny * p->nz / W, p->batch); break;
+    case PK_FILT: pc.grid = dim3((nseq + W - 1) / W, p->batch); break;
+    default: pc.grid = dim3(p->kxn * (p->nz / W), p->batch); break;
+  }
+}
+
+template <typename T>
+double time_kind(ad_ctx* ctx, Plan* p, int method, int kind, int reps) {
+  std::vector<LaunchRec> rec;
+  ctx->record = &rec;
+  Common c;
+  c.st = p->st;
+  c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method; c.cfg.hist = p->hist; c.cfg.hist_ld = p->hist_cap;
+  SolveIO io{p->F0, p->Uscratch, nullptr, method, false};
+  int nl = 0;
+  const ad_status s = enqueue_body<T>(ctx, p, nullptr, io, c, &nl);
+  ctx->record = nullptr;
+  if (s != AD_OK) return -1.0;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return -1.0;
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return -1.0; }
+  double total = 0.0;
+  bool ok = true;
+  for (LaunchRec r : rec) {
+    if (r.kind != kind) continue;
+    r.af.force = r.ad.force = 1;
+    r.af.stage = r.ad.stage = SS_NONE;
+    r.af.set_cond = r.ad.set_cond = r.af.clear_cond = r.ad.clear_cond = 0;
+    auto go = [&]() { return r.f64 ? launch_pass<double>(r.kind, r.E, r.grid, r.threads, r.smem, nullptr, r.ad)
+                                    : launch_pass<float>(r.kind, r.E, r.grid, r.threads, r.smem, nullptr, r.af); };
+    cudaError_t e = go();
+    if (e == cudaSuccess) e = cudaEventRecord(e0, nullptr);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = go();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, nullptr);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) { cudaGetLastError(); ok = false; break; }
+    total += ms / reps;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ok ? total : -1.0;
+}
+
+ad_status autotune_plan(ad_ctx* ctx, Plan* p, int method, int reps) {
+  ad_status s;
+  if ((s = ensure_vectors(ctx, p)) != AD_OK || (s = ensure_hist(ctx, p, 1)) != AD_OK) return s;
+  if (!p->Uscratch && (s = dmalloc(ctx, p, &p->Uscratch, (size_t)p->P * p->batch * (p->f64 ? 8 : 4))) != AD_OK)
+    return s;
+  const int M = p->nx / 2;
+  const int Lf = p->ndim == 3 ? p->nz : p->ny;
+  std::vector<TileSlot> slots = {{&p->xf, PK_XFWD, M, M + 1, pow2_part(p->ny)},
+                                 {&p->xi, PK_XINV, M, M + 1, pow2_part(p->ny)},
+                                 {&p->fl, PK_FILT, Lf, Lf, 0}};
+  if (p->ndim == 3) {
+    slots.push_back({&p->yf, PK_YFWD, p->ny, p->ny, pow2_part(p->nz)});
+    slots.push_back({&p->yi, PK_YINV, p->ny, p->ny, pow2_part(p->nz)});
+  }
+  const size_t cs = p->f64 ? 16 : 8;
+  for (TileSlot& sl : slots) {
+    PassCfg best = *sl.pc;
+    double best_ms = -1.0;
+    for (int W = 1; W <= 4096; W *= 2) {
+      if (sl.div > 0 && sl.div % W != 0) break;
+      const long long tot = (long long)W * sl.L;
+      if (tot % sl.pc->E != 0) continue;
+      const long long T = tot / sl.pc->E;
+      int ld = phys_h(sl.slots - 1) + 1;
+      if ((ld & 1) == 0) ++ld;
+      if (T < 32 || T > 256 || (size_t)W * ld * cs > 100 * 1024) continue;
+      PassCfg trial = *sl.pc;
+      set_tile(p, trial, sl.kind, sl.L, sl.slots, W);
+      if ((sl.kind == PK_XINV || sl.kind == PK_FILT) && trial.grid.x > p->maxblk) continue;
+      const PassCfg keep = *sl.pc;
+      *sl.pc = trial;
+      const double ms = p->f64 ? time_kind<double>(ctx, p, method, sl.kind, reps)
+                               : time_kind<float>(ctx, p, method, sl.kind, reps);
+      *sl.pc = keep;
+      if (ms > 0.0 && (best_ms < 0.0 || ms < best_ms)) { best_ms = ms; best = trial; }
+    }
+    *sl.pc = best;
+  }
+  CK(cudaDeviceSynchronize());
+  drop_graphs(ctx);                 // cached graphs hold the old launch shapes
+  p->tuned = true;
+  return AD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched solve of fields of uneven size: one CUDA graph whose concurrent
+// branches each solve one group of same-shape fields (gathered into the
+// group plan's contiguous buffers, solved with their own while node, then
+// scattered back).
+
+ad_status ensure_io(ad_ctx* ctx, Plan* p) {
+  if (p->Bin) return AD_OK;
+  const size_t vb = (size_t)p->P * p->batch * (p->f64 ? 8 : 4);
+  ad_status s;
+  if ((s = dmalloc(ctx, p, &p->Bin, vb)) != AD_OK || (s = dmalloc(ctx, p, &p->Bout, vb)) != AD_OK) return s;
+  return AD_OK;
+}
+
+ad_status ensure_streams(ad_ctx* ctx, size_t n) {
+  while (ctx->branches.size() < n) {
+    cudaStream_t s;
+    cudaEvent_t e1, e2;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    ctx->branches.push_back(s);
+    CK(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+    ctx->events.push_back(e1);
+    ctx->events.push_back(e2);
+  }
+  return AD_OK;
+}
+
+template <typename T>
+ad_status capture_group(ad_ctx* ctx, BatchedGroup& gr, cudaStream_t s, cudaGraphConditionalHandle h,
+                        const void* const* ubar, void* const* u_out, int method, double tol, int maxit) {
+  Plan* p = gr.p;
+  Common c;
+  c.st = p->st;
+  c.cfg.tol = tol;
+  c.cfg.maxit = maxit;
+  c.cfg.method = method;
+  c.cfg.hist = p->hist;
+  c.cfg.hist_ld = p->hist_cap;
+  c.cond = h;
+  c.in_graph = true;
+  const size_t bytes = (size_t)p->P * sizeof(T);
+  for (size_t k = 0; k < gr.fields.size(); ++k)
+    CK(cudaMemcpyAsync((char*)p->Bin + k * bytes, ubar[gr.fields[k]], bytes, cudaMemcpyDeviceToDevice, s));
+  SolveIO io{p->Bin, p->Bout, nullptr, method, false};
+  ad_status st = enqueue_init<T>(ctx, p, s, io, c, &gr.n_init);
+  if (st != AD_OK) return st;
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &cg, &deps, nullptr, &nd));
+  cudaGraphNode_t cn = nullptr;
+  cudaGraphNodeParams np{};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = h;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  CK(cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &np));
+  CK(cudaStreamUpdateCaptureDependencies(s, &cn, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  CK(cudaStreamBeginCaptureToGraph(ctx->cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  st = enqueue_body<T>(ctx, p, ctx->cap2, io, c, &gr.n_body);
+  cudaGraph_t bg = nullptr;
+  cudaError_t e = cudaStreamEndCapture(ctx->cap2, &bg);
+  if (st != AD_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaStreamEndCapture(batched body)");
+  if ((st = enqueue_finish<T>(ctx, p, s, io, c, &gr.n_fin)) != AD_OK) return st;
+  for (size_t k = 0; k < gr.fields.size(); ++k)
+    CK(cudaMemcpyAsync(u_out[gr.fields[k]], (char*)p->Bout + k * bytes, bytes, cudaMemcpyDeviceToDevice, s));
+  return AD_OK;
+}
+
+ad_status build_batched(ad_ctx* ctx, BatchedEntry& be, const void* const* ubar, void* const* u_out, int method,
+                        double tol, int maxit) {
+  const size_t G = be.groups.size();
+  ad_status st = ensure_streams(ctx, G);
+  if (st != AD_OK) return st;
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  std::vector<cudaGraphConditionalHandle> hs(G);
+  for (size_t i = 0; i < G; ++i) {
+    cudaError_t e = cudaGraphConditionalHandleCreate(&hs[i], g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaGraphConditionalHandleCreate"); }
+  }
+  cudaError_t e = cudaStreamBeginCaptureToGraph(ctx->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
+  e = cudaEventRecord(ctx->events[0], ctx->cap);
+  if (e != cudaSuccess) st = cuda_fail(ctx, e, "fork event");
+  for (size_t i = 0; i < G && st == AD_OK; ++i) {
+    cudaStream_t bs = ctx->branches[i];
+    e = cudaStreamWaitEvent(bs, ctx->events[0], 0);
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "branch fork"); break; }
+    BatchedGroup& gr = be.groups[i];
+    st = gr.p->f64 ? capture_group<double>(ctx, gr, bs, hs[i], ubar, u_out, method, tol, maxit)
+                   : capture_group<float>(ctx, gr, bs, hs[i], ubar, u_out, method, tol, maxit);
+    if (st != AD_OK) break;
+    e = cudaEventRecord(ctx->events[2 * i + 1], bs);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->cap, ctx->events[2 * i + 1], 0);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "branch join");
+  }
+  cudaGraph_t gout = nullptr;
+  e = cudaStreamEndCapture(ctx->cap, &gout);
+  if (st == AD_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamEndCapture(batched)");
+  if (st != AD_OK) { cudaGetLastError(); cudaGraphDestroy(g); return st; }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaGraphInstantiate(batched)"); }
+  be.g = g;
+  be.exec = exec;
+  return AD_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -695,6 +946,8 @@ void ad_destroy(ad_ctx* c) {
   drop_graphs(c);
   for (auto& kv : c->plans) free_plan(kv.second);
   for (auto& kv : c->tw) cudaFree(kv.second);
+  for (auto s : c->branches) cudaStreamDestroy(s);
+  for (auto e : c->events) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
   delete c;
@@ -752,6 +1005,110 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
   if (ms_per_launch) *ms_per_launch = (double)ms / reps;
   ctx->launches = reps + 1;
   return AD_OK;
+}
+
+ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, const void* const* ubar,
+                                void* const* u_out, ad_method method, double tol, int maxit, int* iterations,
+                                ad_status* status, double* const* res_hist, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  if (nfields < 0) return fail(ctx, AD_ERR_ARG, "nfields < 0");
+  if (nfields == 0) { ctx->launches = 0; return AD_OK; }
+  if (!grids || !ubar || !u_out) return fail(ctx, AD_ERR_ARG, "NULL array argument");
+  if (method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "unknown method");
+  if (maxit < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return fail(ctx, AD_ERR_ARG, "need maxit >= 0 and finite tol >= 0");
+  ad_status s;
+  for (int i = 0; i < nfields; ++i) {
+    if ((s = check_grid(ctx, &grids[i])) != AD_OK) return s;
+    if (!ubar[i] || !u_out[i]) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
+    if (ubar[i] == u_out[i]) return fail(ctx, AD_ERR_ARG, "u_out must not alias ubar");
+    if (((uintptr_t)ubar[i] | (uintptr_t)u_out[i]) & 15) return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  }
+  CK(cudaSetDevice(ctx->device));
+  // group by shape (order of first appearance), one plan per group
+  std::vector<std::string> keys;
+  std::vector<std::vector<int>> members;
+  for (int i = 0; i < nfields; ++i) {
+    const std::string k = plan_key(&grids[i], 0);
+    size_t j = 0;
+    while (j < keys.size() && keys[j] != k) ++j;
+    if (j == keys.size()) { keys.push_back(k); members.emplace_back(); }
+    members[j].push_back(i);
+  }
+  std::string bkey = "B|";
+  char buf[128];
+  snprintf(buf, sizeof buf, "%d|%a|%d|", (int)method, tol, maxit);
+  bkey += buf;
+  std::vector<BatchedGroup> groups(keys.size());
+  for (size_t j = 0; j < keys.size(); ++j) {
+    Plan* p = nullptr;
+    if ((s = get_plan(ctx, &grids[members[j][0]], (int)members[j].size(), &p)) != AD_OK) return s;
+    if ((s = ensure_vectors(ctx, p)) != AD_OK || (s = ensure_io(ctx, p)) != AD_OK) return s;
+    if (ctx->autotune && !p->tuned && (s = autotune_plan(ctx, p, (int)method, 10)) != AD_OK) return s;
+    groups[j].p = p;
+    groups[j].fields = members[j];
+  }
+  // history buffers (may drop cached graphs): size every group first
+  for (auto& gr : groups)
+    if ((s = ensure_hist(ctx, gr.p, maxit)) != AD_OK) return s;
+  for (size_t j = 0; j < groups.size(); ++j) {
+    snprintf(buf, sizeof buf, "%p:", (void*)groups[j].p);
+    bkey += buf;
+    for (int f : groups[j].fields) {
+      snprintf(buf, sizeof buf, "%p>%p,", ubar[f], u_out[f]);
+      bkey += buf;
+    }
+  }
+  auto it = ctx->bgraphs.find(bkey);
+  if (it == ctx->bgraphs.end()) {
+    BatchedEntry be;
+    be.groups = groups;
+    if ((s = build_batched(ctx, be, ubar, u_out, (int)method, tol, maxit)) != AD_OK) return s;
+    it = ctx->bgraphs.emplace(bkey, be).first;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaGraphLaunch(it->second.exec, st));
+  std::vector<std::vector<FieldState>> hs(it->second.groups.size());
+  for (size_t j = 0; j < it->second.groups.size(); ++j) {
+    const BatchedGroup& gr = it->second.groups[j];
+    hs[j].resize(gr.fields.size());
+    CK(cudaMemcpyAsync(hs[j].data(), gr.p->st, sizeof(FieldState) * gr.fields.size(), cudaMemcpyDeviceToHost, st));
+    if (res_hist)
+      for (size_t k = 0; k < gr.fields.size(); ++k)
+        if (res_hist[gr.fields[k]])
+          CK(cudaMemcpyAsync(res_hist[gr.fields[k]], gr.p->hist + k * (size_t)gr.p->hist_cap,
+                             sizeof(double) * (size_t)(maxit + 1), cudaMemcpyDeviceToHost, st));
+  }
+  CK(cudaStreamSynchronize(st));
+  ad_status worst = AD_OK;
+  int64_t launches = 0;
+  for (size_t j = 0; j < it->second.groups.size(); ++j) {
+    const BatchedGroup& gr = it->second.groups[j];
+    int maxpass = 0;
+    for (size_t k = 0; k < gr.fields.size(); ++k) {
+      const FieldState& f = hs[j][k];
+      const int i = gr.fields[k];
+      if (iterations) iterations[i] = f.iter;
+      if (status) status[i] = (ad_status)f.status;
+      if (worst == AD_OK && f.status != AD_OK) worst = (ad_status)f.status;
+      maxpass = std::max(maxpass, f.iter + (f.status == AD_BREAKDOWN ? 1 : 0));
+    }
+    launches += gr.n_init + gr.n_fin + (int64_t)std::max(1, maxpass) * gr.n_body;
+  }
+  ctx->launches = launches;
+  return worst;
+}
+
+ad_status ad_autotune(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method method, int enable_for_batched) {
+  if (!ctx) return AD_ERR_ARG;
+  ctx->autotune = enable_for_batched != 0;
+  if (!grid) return AD_OK;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 1 || method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "bad batch or method");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
+  return autotune_plan(ctx, p, (int)method, 10);
 }
 
 ad_status ad_set_graph_mode(ad_ctx* c, int enable) {
