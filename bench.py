@@ -176,6 +176,68 @@ def _golden_count(method, seed):
     return None
 
 
+def _timed(fn):
+    import torch
+    fn()                                            # warm-up (plans, graphs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = fn()
+    torch.cuda.synchronize()
+    return r, time.perf_counter() - t0
+
+
+def _extra_workloads(gad, dev, extras):
+    """Other workloads of the method, one timed solve each after a warm-up:
+    the 3D velocity (256^3 x 3 components, gamma = 0.1, BiCGSTAB per
+    component to 1e-6) and the uneven batch (48 seeded sizes, 2D 256..4096
+    and 3D 64..384, gamma by grid size, BiCGSTAB to 1e-6 in one batched call,
+    against the same fields solved one shape group at a time)."""
+    import torch
+    from synth import fields
+    out = {}
+    if "3d256" in extras:
+        n = 256
+        v = fields.random_velocity_field((n, n, n), 0, fields.spectrum_3d_kolmogorov).astype(np.float32)
+        u_true = torch.from_numpy(v).to(dev)
+        ub = gad.filter(u_true, 0.1, ndim=3)
+        del u_true
+        r, t = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3))
+        its = [int(x) for x in r.iterations]
+        out["velocity3d_256_f32"] = {"mpoints_s": 3 * n ** 3 / t / 1e6, "ms": t * 1e3, "iterations": its,
+                                     "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches}
+        del ub, r
+        torch.cuda.empty_cache()
+    if "uneven48" in extras:
+        shapes = fields.uneven_batch(0)
+        ub, gammas = [], []
+        for i, sh in enumerate(shapes):
+            spec = _spectrum if len(sh) == 2 else fields.spectrum_3d_kolmogorov
+            g = fields.gamma_for_grid(sh)
+            ub.append(gad.filter(fields.random_scalar_field_torch(sh, 1000 + i, spec, device=dev), g, ndim=len(sh)))
+            gammas.append(g)
+        pts = float(sum(np.prod(sh) for sh in shapes))
+        res, t = _timed(lambda: gad.deconvolve_batched(ub, gammas, method="bicgstab", tol=1e-6, maxit=3000,
+                                                       history=False))
+        its = res[1]
+        launches = gad.last_launch_count()
+        # the same fields, one shape group per call
+        groups = {}
+        for i, sh in enumerate(shapes):
+            groups.setdefault(sh, []).append(i)
+
+        def seq():
+            for sh, idx in groups.items():
+                stacked = torch.stack([ub[i] for i in idx])
+                gad.deconvolve(stacked, gammas[idx[0]], method="bicgstab", tol=1e-6, maxit=3000, ndim=len(sh),
+                               history=False)
+        _, t_seq = _timed(seq)
+        out["uneven48_f32"] = {"mpoints_s": pts / t / 1e6, "ms": t * 1e3, "points": pts, "fields": len(shapes),
+                               "shape_groups": len(groups), "iterations_mean": float(np.mean(its)),
+                               "converged": bool(np.all(res[2] == gad.AD_OK)), "launches": launches,
+                               "one_call_per_group_mpoints_s": pts / t_seq / 1e6}
+    return out
+
+
 def run_reference(args):
     """The CPU oracle timed on the host cores: each step is one BiCGSTAB pass
     over one 2048^2 field; the metric extrapolates the per-pass time to the
@@ -222,6 +284,8 @@ def main():
                     help="drive the iteration loop from the host instead of a graph while node (same kernels; "
                          "profilers cannot see kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="fields per GPU")
+    ap.add_argument("--extras", default="methods,3d256,uneven48",
+                    help="comma list of extra measurements on rank 0: methods, 3d256, uneven48")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -323,7 +387,8 @@ def main():
             "iterations": {"min": min(iters), "max": max(iters), "mean": float(np.mean(iters))},
             "converged": ok, "e2e": e2e, "gpu_launches": int(launches), "clocks": clocks}
 
-    if rank == 0 and not args.no_extras:
+    extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
+    if rank == 0 and "methods" in extras:
         # comparison methods on the same batch (one timed solve each)
         methods = {}
         for m, mi in (("cg", 3000), ("bicgstab", 3000), ("vancittert", VC_MAXIT)):
@@ -345,6 +410,7 @@ def main():
                 methods[m]["maxit"] = VC_MAXIT
         line["methods"] = methods
 
+    if rank == 0 and not args.no_extras:
         # roofline of the dominant pass kernel, timed live with CUDA events
         passes = gad.time_passes(n, gamma, B, method=args.method, reps=20)
         kxn = n[1] // 2 + 1
@@ -382,6 +448,10 @@ def main():
                                            "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
                                            "extrapolated to the %d passes the GPU solve of that field needed"
                                            % (args.method, t0, sample_passes, per, n0))}
+    if rank == 0 and (extras & {"3d256", "uneven48"}):
+        del out, dev_in, host_out
+        torch.cuda.empty_cache()
+        line["workloads"] = _extra_workloads(gad, dev, extras)
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:

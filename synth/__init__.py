@@ -15,4 +15,6 @@ from .fields import (  # noqa: F401
     shell_spectrum,
     gamma_for_grid,
     WORKLOADS,
+    smooth_sizes,
+    uneven_batch,
 )

@@ -130,6 +130,33 @@ def gamma_for_grid(shape):
     return 0.01 if max(shape) >= 512 else 0.1
 
 
+def smooth_sizes(lo, hi):
+    """Even sides of the form 2^a 3^b (a >= 2, b <= 2) in [lo, hi]."""
+    out = []
+    for b in range(3):
+        for a in range(2, 20):
+            n = 2 ** a * 3 ** b
+            if lo <= n <= hi:
+                out.append(n)
+    return sorted(out)
+
+
+def uneven_batch(seed=0, n2d=24, n3d=24):
+    """Grid shapes for a batch of uneven fields: sides drawn log-uniformly
+    (numpy PCG64, `seed`) in [256, 4096] (2D) and [64, 384] (3D), each
+    snapped to the nearest side in log space among smooth_sizes. Returns a
+    list of shapes, 2D first, in draw order."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    for count, lo, hi, nd in ((n2d, 256, 4096, 2), (n3d, 64, 384, 3)):
+        cand = np.array(smooth_sizes(lo, hi), dtype=np.float64)
+        for _ in range(count):
+            x = np.exp(rng.uniform(np.log(lo), np.log(hi)))
+            n = int(cand[np.argmin(np.abs(np.log(cand) - np.log(x)))])
+            shapes.append((n,) * nd)
+    return shapes
+
+
 # Named workloads (shapes, spectra, filter strengths, solver settings).
 WORKLOADS = {
     "vorticity2d_128_f64": dict(
@@ -149,3 +176,33 @@ WORKLOADS = {
         spectrum=lambda k: spectrum_2d_kraichnan(k, kp=10.0, kcut=600.0),
         tol=1e-6, methods=("bicgstab",)),
 }
+
+
+def random_scalar_field_torch(shape, seed, spectrum, device="cuda"):
+    """The recipe of random_scalar_field (white noise shaped to the shell
+    spectrum, mean removed, unit RMS) evaluated with torch on a device, for
+    benchmark inputs too large to draw on the host. Seeded by a torch
+    generator, so the field differs from the NumPy one with the same seed."""
+    import torch
+    shape = tuple(int(n) for n in shape)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    w = torch.randn(shape, generator=g, device=device, dtype=torch.float64)
+    axes = []
+    for d, n in enumerate(shape):
+        f = torch.fft.rfftfreq(n, d=1.0 / n) if d == len(shape) - 1 else torch.fft.fftfreq(n, d=1.0 / n)
+        axes.append(f.to(device=device, dtype=torch.float64))
+    k2 = None
+    for d, f in enumerate(axes):
+        view = [1] * len(shape)
+        view[d] = -1
+        t = f.reshape(view) ** 2
+        k2 = t if k2 is None else k2 + t
+    kmag = torch.sqrt(k2)
+    shell = (2.0 * math.pi * kmag) if len(shape) == 2 else (4.0 * math.pi * kmag * kmag)
+    e = torch.as_tensor(spectrum(kmag.cpu().numpy()), device=device)
+    amp = torch.where(kmag > 0, torch.sqrt(e / torch.where(kmag > 0, shell, torch.ones_like(shell))),
+                      torch.zeros_like(kmag))
+    u = torch.fft.irfftn(torch.fft.rfftn(w) * amp, s=shape)
+    u = u - u.mean()
+    return (u / torch.sqrt(torch.mean(u * u))).float()

@@ -44,3 +44,13 @@ def test_gamma_rule():
     assert fields.gamma_for_grid((256, 256)) == 0.1
     assert fields.gamma_for_grid((512, 512, 512)) == 0.01
     assert fields.gamma_for_grid((64, 64, 64)) == 0.1
+
+
+def test_uneven_batch_sizes():
+    shapes = fields.uneven_batch(0)
+    assert len(shapes) == 48
+    assert all(len(s) == 2 and 256 <= s[0] <= 4096 for s in shapes[:24])
+    assert all(len(s) == 3 and 64 <= s[0] <= 384 for s in shapes[24:])
+    ok = set(fields.smooth_sizes(64, 4096))
+    assert all(s[0] in ok and s[0] % 4 == 0 for s in shapes)
+    assert shapes == fields.uneven_batch(0) and shapes != fields.uneven_batch(1)
