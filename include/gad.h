@@ -127,6 +127,44 @@ ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, 
                                 void* const* u_out, ad_method method, double tol, int maxit, int* iterations,
                                 ad_status* status, double* const* res_hist, void* stream);
 
+/* Learned initial guess for BiCGSTAB (no counterpart in the paper): a bias-free
+ * 3x3x3 convolutional network with periodic padding, channels 1 -> 32 -> 32 ->
+ * 32 -> 1, ReLU after the first three layers, applied to u_bar / sigma
+ * (sigma = RMS of u_bar) with residual output u0 = u_bar + sigma * A * y,
+ * A = 1/(pi gamma)^2 = (delta/h)^2 taken from the grid's gamma; pass u0 to
+ * ad_deconvolve. bfloat16 activations, float32 accumulation (tensor cores
+ * for the 32 -> 32 layers). Fields: 3D float32, Nx a multiple of 32.
+ * Weights: float32 array of ad_guess_weight_count() values, layout
+ *   W1[27][32], W2[27][32][32], W3[27][32][32], W4[27][32]  (tap, in, out),
+ *   tap = (a*3 + b)*3 + c weighting the input at (z+a-1, y+b-1, x+c-1).
+ * All field and weight pointers are device pointers unless stated. */
+int64_t ad_guess_weight_count(void);
+
+/* Initial weights into a HOST array of n = ad_guess_weight_count() floats,
+ * from a splitmix64 stream seeded by seed. stencil = 0: He-normal (last layer
+ * scaled by 0.1). stencil != 0: the explicit local inverse of G,
+ * u0 = u_bar - (delta/h)^2 L_h u_bar with the 7-point Laplacian L_h (channels
+ * 0 and 1 carry +L and -L through the ReLUs), every other weight He-normal
+ * scaled by 1e-3, so training starts from that approximation. */
+ad_status ad_guess_init(float* weights_host, int64_t n, uint64_t seed, int stencil);
+
+/* u0 = u_bar + sigma * CNN(u_bar / sigma) for `batch` fields. */
+ad_status ad_guess_infer(ad_ctx* ctx, const ad_grid* grid, const float* weights, const float* ubar, float* u0,
+                         int batch, void* stream);
+
+/* Loss (host double, batch mean of ||u0 - u_true||^2 / ||u_true||^2) and its
+ * gradient with respect to the weights (device float array) for one batch. */
+ad_status ad_guess_grad(ad_ctx* ctx, const ad_grid* grid, const float* weights, const float* ubar,
+                        const float* utrue, int batch, float* grad, double* loss, void* stream);
+
+/* Trains the weights in place with Adam (lr, beta1 0.9, beta2 0.999) for
+ * `epochs` passes over `npairs` (u_bar, u_true) pairs ([npairs][P] device
+ * arrays) in minibatches of `batch` drawn by a seeded shuffle; loss_hist
+ * (host double[epochs], may be NULL) receives each epoch's mean loss. */
+ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const float* ubar, const float* utrue,
+                         int epochs, int batch, double lr, uint64_t seed, float* weights, double* loss_hist,
+                         void* stream);
+
 /* Tile autotuner. With `grid` non-NULL, tunes the plan for (grid, batch):
  * for every pass of one iteration of `method` it times each admissible tile
  * width (32-256 threads per block, <= 100 KB shared memory) with CUDA events

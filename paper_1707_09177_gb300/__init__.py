@@ -32,7 +32,8 @@ AD_F32, AD_F64 = 0, 1
 
 EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvolve_batched", "ad_time_pass",
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
-            "ad_filter_static")
+            "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
+            "ad_guess_train")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv"}
 
 
@@ -79,6 +80,17 @@ def load(path=None):
     lib.ad_deconvolve_batched.argtypes = [c_p, c_i, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_d, c_i, c_p, c_p,
                                           c_p, c_p]
     lib.ad_deconvolve_batched.restype = c_i
+    lib.ad_guess_weight_count.argtypes = []
+    lib.ad_guess_weight_count.restype = ctypes.c_int64
+    lib.ad_guess_init.argtypes = [c_p, ctypes.c_int64, ctypes.c_uint64, c_i]
+    lib.ad_guess_init.restype = c_i
+    lib.ad_guess_infer.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_p, c_i, c_p]
+    lib.ad_guess_infer.restype = c_i
+    lib.ad_guess_grad.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_p, c_i, c_p, c_p, c_p]
+    lib.ad_guess_grad.restype = c_i
+    lib.ad_guess_train.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_p, c_p, c_i, c_i, c_d, ctypes.c_uint64,
+                                   c_p, c_p, c_p]
+    lib.ad_guess_train.restype = c_i
     lib.ad_autotune.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_i]
     lib.ad_autotune.restype = c_i
     lib.ad_time_pass.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_i, c_i, c_p, c_p, c_p, c_p, c_p]
@@ -290,3 +302,65 @@ def autotune(shape=None, gamma=0.1, batch=1, method="bicgstab", dtype="f32", for
     st = lib.ad_autotune(ctx, ctypes.byref(g) if g is not None else None, int(batch), METHODS[method],
                          1 if for_batched else 0)
     _check(st, ctx)
+
+
+# --- learned initial guess ------------------------------------------------------
+
+def guess_init(seed=0, stencil=True, device=None):
+    """Initial network weights as a float32 CUDA tensor: the explicit local
+    inverse stencil (default) or He-normal."""
+    import torch
+    lib = load()
+    n = int(lib.ad_guess_weight_count())
+    w = np.zeros(n, dtype=np.float32)
+    st = lib.ad_guess_init(ctypes.c_void_p(w.ctypes.data), n, int(seed), 1 if stencil else 0)
+    if st != AD_OK:
+        raise GadError(st, "ad_guess_init")
+    return torch.from_numpy(w).to("cuda" if device is None else device)
+
+
+def _guess_grid(t, gamma):
+    g, b, _ = _grid(t, 3, gamma)
+    return g, b
+
+
+def guess_infer(weights, ubar, gamma, out=None, stream=None):
+    """u0 = u_bar + sigma A CNN(u_bar / sigma) for 3D float32 fields (batch first)."""
+    import torch
+    lib = load()
+    ctx = context(ubar.device.index)
+    g, b = _guess_grid(ubar, gamma)
+    out = torch.empty_like(ubar) if out is None else out
+    st = lib.ad_guess_infer(ctx, ctypes.byref(g), ctypes.c_void_p(weights.data_ptr()),
+                            ctypes.c_void_p(ubar.data_ptr()), ctypes.c_void_p(out.data_ptr()), b, _stream_ptr(stream))
+    _check(st, ctx)
+    return out
+
+
+def guess_grad(weights, ubar, utrue, gamma, stream=None):
+    """(loss, gradient) of the batch-mean relative MSE for one batch."""
+    import torch
+    lib = load()
+    ctx = context(ubar.device.index)
+    g, b = _guess_grid(ubar, gamma)
+    grad = torch.empty_like(weights)
+    loss = ctypes.c_double(0.0)
+    st = lib.ad_guess_grad(ctx, ctypes.byref(g), ctypes.c_void_p(weights.data_ptr()), ctypes.c_void_p(ubar.data_ptr()),
+                           ctypes.c_void_p(utrue.data_ptr()), b, ctypes.c_void_p(grad.data_ptr()), ctypes.byref(loss),
+                           _stream_ptr(stream))
+    _check(st, ctx)
+    return loss.value, grad
+
+
+def guess_train(weights, ubar, utrue, gamma, epochs=20, batch=8, lr=2e-5, seed=0, stream=None):
+    """Trains ``weights`` (updated in place) on pairs [npairs, Z, Y, X]; returns
+    the per-epoch mean losses."""
+    lib = load()
+    ctx = context(ubar.device.index)
+    g, n = _guess_grid(ubar, gamma)
+    hist = np.zeros(max(int(epochs), 1))
+    st = lib.ad_guess_train(ctx, ctypes.byref(g), n, ctypes.c_void_p(ubar.data_ptr()), ctypes.c_void_p(utrue.data_ptr()),
+                            int(epochs), int(batch), float(lr), int(seed), ctypes.c_void_p(weights.data_ptr()),
+                            ctypes.c_void_p(hist.ctypes.data), _stream_ptr(stream))
+    _check(st, ctx)
+    return hist[: int(epochs)]

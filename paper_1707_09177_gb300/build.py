@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgad.so")
-SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -23,6 +23,7 @@
 
 #include "../../include/gad.h"
 #include "args.h"
+#include "cnn.h"
 #include "launch.h"
 #include "state.h"
 
@@ -104,7 +105,18 @@ struct BatchedEntry {
   std::vector<BatchedGroup> groups;
 };
 
+struct CnnWork {
+  gad::CnnBuffers w;
+  std::vector<void*> owned;
+  float* ub = nullptr;          // training minibatch gathers
+  float* ut = nullptr;
+  float* u0 = nullptr;
+  double* losses = nullptr;     // per minibatch
+  int nloss = 0;
+};
+
 struct ad_ctx {
+  std::map<std::string, CnnWork*> cnn;        // learned-guess workspaces by (shape, batch)
   bool autotune = false;                      // tune the tiles of every new plan of a batched solve
   std::vector<LaunchRec>* record = nullptr;   // when set, pass launches are recorded, not issued
   std::map<std::string, BatchedEntry> bgraphs;
@@ -802,6 +814,87 @@ ad_status autotune_plan(ad_ctx* ctx, Plan* p, int method, int reps) {
 }
 
 // ---------------------------------------------------------------------------
+// Learned initial guess (cnn.cu): workspaces and checks.
+
+ad_status check_cnn_grid(ad_ctx* ctx, const ad_grid* g) {
+  ad_status s = check_grid(ctx, g);
+  if (s != AD_OK) return s;
+  if (g->ndim != 3 || g->dtype != AD_F32) return fail(ctx, AD_ERR_ARG, "the learned guess takes 3D float32 fields");
+  if (!cnn_shape_ok((int)g->n[0], (int)g->n[1], (int)g->n[2]))
+    return fail(ctx, AD_ERR_ARG, "the learned guess needs Nx a multiple of 32");
+  return AD_OK;
+}
+
+ad_status cnn_alloc(ad_ctx* ctx, CnnWork* cw, void** out, size_t bytes) {
+  if (cudaMalloc(out, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(ctx, AD_ERR_NOMEM, "learned-guess workspace of " + std::to_string(bytes) + " bytes");
+  }
+  cw->owned.push_back(*out);
+  return AD_OK;
+}
+
+// Workspace for (X, Y, Z, B); `training` adds gradients, moments and gathers.
+ad_status get_cnn(ad_ctx* ctx, const ad_grid* g, int B, bool training, CnnWork** out) {
+  char key[128];
+  snprintf(key, sizeof key, "%lld:%lld:%lld:%d", (long long)g->n[0], (long long)g->n[1], (long long)g->n[2], B);
+  auto it = ctx->cnn.find(key);
+  CnnWork* cw = it == ctx->cnn.end() ? nullptr : it->second;
+  if (!cw) {
+    cw = new CnnWork;
+    ctx->cnn[key] = cw;
+  }
+  const size_t P = (size_t)g->n[0] * g->n[1] * g->n[2];
+  const size_t act = sizeof(__nv_bfloat16) * P * 32 * B, frag = sizeof(uint2) * 27 * 2 * 4 * 32;
+  ad_status s;
+  gad::CnnBuffers& w = cw->w;
+  if (!w.master) {
+    if ((s = cnn_alloc(ctx, cw, (void**)&w.master, sizeof(float) * kCnnWeights)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.frag2, frag)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.frag3, frag)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.frag2t, frag)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.frag3t, frag)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.H1, act)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.H2, act)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.H3, act)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.sumsq, sizeof(double) * (2 * B + 1))) != AD_OK)
+      return s;
+  }
+  if (training && !w.grad) {
+    if ((s = cnn_alloc(ctx, cw, (void**)&w.grad, sizeof(float) * kCnnWeights)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.m, sizeof(float) * kCnnWeights)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.v, sizeof(float) * kCnnWeights)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.dA, act)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.dB, act)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.g, sizeof(float) * P * B)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.part, sizeof(float) * (size_t)kCnnPartFloats)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&cw->ub, sizeof(float) * P * B)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&cw->ut, sizeof(float) * P * B)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&cw->u0, sizeof(float) * P * B)) != AD_OK)
+      return s;
+  }
+  *out = cw;
+  return AD_OK;
+}
+
+// A = (delta/h)^2 = 1/(pi gamma)^2: delta = 1/k_c, k_c = gamma N/2, h = 2 pi/N
+double cnn_ascale(double gamma) { return 1.0 / ((3.141592653589793 * gamma) * (3.141592653589793 * gamma)); }
+
+// splitmix64 (Steele, Lea, Flood 2014) and a Box-Muller normal, host side
+uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+double normal01(uint64_t& st) {
+  const double u1 = ((splitmix64(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  const double u2 = ((splitmix64(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+// ---------------------------------------------------------------------------
 // Batched solve of fields of uneven size: one CUDA graph whose concurrent
 // branches each solve one group of same-shape fields (gathered into the
 // group plan's contiguous buffers, solved with their own while node, then
@@ -945,6 +1038,10 @@ void ad_destroy(ad_ctx* c) {
   cudaDeviceSynchronize();
   drop_graphs(c);
   for (auto& kv : c->plans) free_plan(kv.second);
+  for (auto& kv : c->cnn) {
+    for (void* q : kv.second->owned) cudaFree(q);
+    delete kv.second;
+  }
   for (auto& kv : c->tw) cudaFree(kv.second);
   for (auto s : c->branches) cudaStreamDestroy(s);
   for (auto e : c->events) cudaEventDestroy(e);
@@ -1109,6 +1206,146 @@ ad_status ad_autotune(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method met
   Plan* p = nullptr;
   if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
   return autotune_plan(ctx, p, (int)method, 10);
+}
+
+int64_t ad_guess_weight_count(void) { return kCnnWeights; }
+
+ad_status ad_guess_init(float* w, int64_t n, uint64_t seed, int stencil) {
+  if (!w || n != kCnnWeights) return AD_ERR_ARG;
+  uint64_t st = seed;
+  const int fan_in[4] = {27, 27 * 32, 27 * 32, 27 * 32};
+  const int off[5] = {kW1, kW2, kW3, kW4, kCnnWeights};
+  for (int l = 0; l < 4; ++l) {
+    double std_ = std::sqrt(2.0 / fan_in[l]);
+    if (stencil) std_ *= 1e-3;
+    else if (l == 3) std_ *= 0.1;
+    for (int i = off[l]; i < off[l + 1]; ++i) w[i] = (float)(std_ * normal01(st));
+  }
+  if (stencil) {
+    // the explicit inverse u0 = u_bar - (delta/h)^2 L_h u_bar with the 7-point
+    // Laplacian L_h: layer 1 forms +L and -L (channels 0, 1), layers 2-3 pass
+    // them on, layer 4 takes -(relu(L) - relu(-L)) = -L (the output scale is A)
+    const int centre = 13;
+    const int faces[6] = {4, 22, 10, 16, 12, 14};       // z-1, z+1, y-1, y+1, x-1, x+1
+    for (int t = 0; t < 27; ++t) w[kW1 + t * 32 + 0] = w[kW1 + t * 32 + 1] = 0.f;
+    w[kW1 + centre * 32 + 0] = -6.f;
+    w[kW1 + centre * 32 + 1] = 6.f;
+    for (int f : faces) {
+      w[kW1 + f * 32 + 0] = 1.f;
+      w[kW1 + f * 32 + 1] = -1.f;
+    }
+    for (int l : {kW2, kW3})             // channels 0, 1 receive only themselves (centre tap)
+      for (int t = 0; t < 27; ++t)
+        for (int ci = 0; ci < 32; ++ci)
+          for (int co = 0; co < 2; ++co) w[l + (t * 32 + ci) * 32 + co] = (t == centre && ci == co) ? 1.f : 0.f;
+    for (int t = 0; t < 27; ++t) w[kW4 + t * 32 + 0] = w[kW4 + t * 32 + 1] = 0.f;
+    w[kW4 + centre * 32 + 0] = -1.f;
+    w[kW4 + centre * 32 + 1] = 1.f;
+  }
+  return AD_OK;
+}
+
+ad_status ad_guess_infer(ad_ctx* ctx, const ad_grid* grid, const float* weights, const float* ubar, float* u0,
+                         int batch, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_cnn_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 0) return fail(ctx, AD_ERR_ARG, "batch < 0");
+  if (batch == 0) return AD_OK;
+  if (!weights || !ubar || !u0) return fail(ctx, AD_ERR_ARG, "NULL pointer");
+  CK(cudaSetDevice(ctx->device));
+  CnnWork* cw = nullptr;
+  if ((s = get_cnn(ctx, grid, batch, false, &cw)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(cw->w.master, weights, sizeof(float) * kCnnWeights, cudaMemcpyDeviceToDevice, st));
+  CK(cnn_pack(cw->w, st));
+  CK(cnn_forward(cw->w, ubar, u0, nullptr, (int)grid->n[0], (int)grid->n[1], (int)grid->n[2], batch,
+                 cnn_ascale(grid->gamma), st));
+  ctx->launches = 4 + 5 + 1;
+  return AD_OK;
+}
+
+ad_status ad_guess_grad(ad_ctx* ctx, const ad_grid* grid, const float* weights, const float* ubar, const float* utrue,
+                        int batch, float* grad, double* loss, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_cnn_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 1 || !weights || !ubar || !utrue || !grad) return fail(ctx, AD_ERR_ARG, "bad batch or NULL pointer");
+  CK(cudaSetDevice(ctx->device));
+  CnnWork* cw = nullptr;
+  if ((s = get_cnn(ctx, grid, batch, true, &cw)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int X = (int)grid->n[0], Y = (int)grid->n[1], Z = (int)grid->n[2];
+  CK(cudaMemcpyAsync(cw->w.master, weights, sizeof(float) * kCnnWeights, cudaMemcpyDeviceToDevice, st));
+  CK(cnn_pack(cw->w, st));
+  CK(cnn_forward(cw->w, ubar, cw->u0, utrue, X, Y, Z, batch, cnn_ascale(grid->gamma), st));
+  CK(cnn_backward(cw->w, ubar, X, Y, Z, batch, st));
+  CK(cudaMemcpyAsync(grad, cw->w.grad, sizeof(float) * kCnnWeights, cudaMemcpyDeviceToDevice, st));
+  double l = 0.0;
+  CK(cudaMemcpyAsync(&l, cw->w.sumsq + 2 * batch, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (loss) *loss = l;
+  return AD_OK;
+}
+
+ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const float* ubar, const float* utrue,
+                         int epochs, int batch, double lr, uint64_t seed, float* weights, double* loss_hist,
+                         void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_cnn_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (npairs < 1 || batch < 1 || batch > npairs || epochs < 0 || !(lr > 0.0) || !ubar || !utrue || !weights)
+    return fail(ctx, AD_ERR_ARG, "bad training arguments");
+  CK(cudaSetDevice(ctx->device));
+  CnnWork* cw = nullptr;
+  if ((s = get_cnn(ctx, grid, batch, true, &cw)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int X = (int)grid->n[0], Y = (int)grid->n[1], Z = (int)grid->n[2];
+  const size_t P = (size_t)X * Y * Z;
+  const int nmb = npairs / batch;
+  if (cw->nloss < nmb) {
+    if (cw->losses) cudaFree(cw->losses);
+    for (auto& q : cw->owned) if (q == cw->losses) q = nullptr;
+    cw->losses = nullptr;
+    if ((s = cnn_alloc(ctx, cw, (void**)&cw->losses, sizeof(double) * nmb)) != AD_OK) return s;
+    cw->nloss = nmb;
+  }
+  CK(cudaMemcpyAsync(cw->w.master, weights, sizeof(float) * kCnnWeights, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(cw->w.m, 0, sizeof(float) * kCnnWeights, st));
+  CK(cudaMemsetAsync(cw->w.v, 0, sizeof(float) * kCnnWeights, st));
+  std::vector<int> order(npairs);
+  for (int i = 0; i < npairs; ++i) order[i] = i;
+  uint64_t rs = seed;
+  std::vector<double> lh(nmb);
+  int step = 0;
+  int64_t launches = 0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    for (int i = npairs - 1; i > 0; --i) std::swap(order[i], order[(int)(splitmix64(rs) % (uint64_t)(i + 1))]);
+    for (int mb = 0; mb < nmb; ++mb) {
+      for (int k = 0; k < batch; ++k) {
+        const size_t src = (size_t)order[mb * batch + k] * P;
+        CK(cudaMemcpyAsync(cw->ub + k * P, ubar + src, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(cw->ut + k * P, utrue + src, sizeof(float) * P, cudaMemcpyDeviceToDevice, st));
+      }
+      CK(cnn_pack(cw->w, st));
+      CK(cnn_forward(cw->w, cw->ub, cw->u0, cw->ut, X, Y, Z, batch, cnn_ascale(grid->gamma), st));
+      CK(cnn_backward(cw->w, cw->ub, X, Y, Z, batch, st));
+      CK(cnn_adam(cw->w, ++step, (float)lr, st));
+      CK(cudaMemcpyAsync(cw->losses + mb, cw->w.sumsq + 2 * batch, sizeof(double), cudaMemcpyDeviceToDevice, st));
+      launches += 4 + 6 + 11 + 1;
+    }
+    if (loss_hist) {
+      CK(cudaMemcpyAsync(lh.data(), cw->losses, sizeof(double) * nmb, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      double m = 0.0;
+      for (double v : lh) m += v;
+      loss_hist[ep] = m / nmb;
+    }
+  }
+  CK(cudaMemcpyAsync(weights, cw->w.master, sizeof(float) * kCnnWeights, cudaMemcpyDeviceToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->launches = launches;
+  return AD_OK;
 }
 
 ad_status ad_set_graph_mode(ad_ctx* c, int enable) {

@@ -1,0 +1,597 @@
+// Learned initial guess for BiCGSTAB: a four-layer bias-free 3x3x3 CNN with
+// periodic padding, channels 1 -> 32 -> 32 -> 32 -> 1, ReLU after the first
+// three layers, applied to u_bar / sigma (sigma = RMS of u_bar) with residual
+// output u0 = u_bar + sigma * y. The paper has no learned component; the
+// network supplies the starting point of Algorithm 4.
+//
+// Activations are bfloat16, channels-last: H[b][p][32], p = (z*Y + y)*X + x.
+// The 32 -> 32 layers are implicit GEMMs on the tensor cores (bf16 inputs,
+// float32 accumulation): for an x-segment of 32 points per warp, the product
+// over K = 27 taps x 32 input channels into N = 32 output channels. The 1-channel
+// first and last layers run on the CUDA cores (the first one in float32, so the
+// small differences it forms from u_bar are not lost to bfloat16 rounding). The
+// output is scaled by the fixed factor A = (delta/h)^2 = 1/(pi gamma)^2, the
+// grid-unit weight of the Laplacian in G^{-1} = I - delta^2 Laplacian (Eq. df):
+// u0 = u_bar + sigma * A * y. Training keeps float32 master
+// weights and Adam moments; the loss is the relative mean-square error
+// ||u0 - u_true||^2 / ||u_true||^2 averaged over the samples of a batch.
+//
+// Weight layout of the float32 master array (kCnnWeights floats):
+//   W1 [27][32]        tap, out channel       (layer 1, in channel 1)
+//   W2 [27][32][32]    tap, in, out
+//   W3 [27][32][32]    tap, in, out
+//   W4 [27][32]        tap, in channel        (layer 4, out channel 1)
+// tap = (a*3 + b)*3 + c multiplies x at (z + a - 1, y + b - 1, x + c - 1).
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "cnn.h"
+
+namespace gad {
+
+namespace {
+
+constexpr int C = 32;
+constexpr int TAPS = 27;
+
+__device__ __forceinline__ int wrap(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* p) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(p));
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(s));
+}
+
+// Row of a shared-memory point tile: 32 bf16 channels (64 bytes) + 16 bytes of
+// padding, so the 8-row ldmatrix phases hit distinct banks.
+constexpr int ROWB = 80;
+
+// Copies the x-segment [x0 - 1, x0 + TX + 1) (periodic) of activation row
+// (b, z, y) into `dst` (TX + 2 rows of ROWB bytes), 16 bytes per thread step.
+__device__ __forceinline__ void load_row(unsigned char* dst, const __nv_bfloat16* H, long long rowbase, int X,
+                                         int x0, int TX, int tid, int nthr) {
+  const int n16 = (TX + 2) * 4;
+  for (int i = tid; i < n16; i += nthr) {
+    const int pt = i >> 2, q = i & 3;
+    const int x = wrap(x0 - 1 + pt, X);
+    const uint4 v = *reinterpret_cast<const uint4*>(H + (rowbase + x) * C + q * 8);
+    *reinterpret_cast<uint4*>(dst + pt * ROWB + q * 16) = v;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// 32 -> 32 convolution on the tensor cores. One warp computes 32 consecutive
+// x points (two m16 tiles) x 32 output channels (four n8 tiles); a block holds
+// TX/32 warps over an x-segment of TX points of one (b, z, y) row and stages
+// the neighbour rows (periodic) in shared memory, three at a time. Weights come in mma
+// B-fragment order (see k_pack_frag) from global memory (L1-resident).
+// mode 0: out = bf16(relu(acc));  mode 1: out = bf16(acc * (mask > 0)).
+__global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16* __restrict__ Hin,
+                                                  const uint2* __restrict__ Wf, __nv_bfloat16* __restrict__ Hout,
+                                                  const __nv_bfloat16* __restrict__ Hmask, int X, int Y, int Z,
+                                                  int TX, int mode) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int segs = X / TX;
+  int r = blockIdx.x;
+  const int seg = r % segs;
+  r /= segs;
+  const int y = r % Y, z = r / Y;
+  const int b = blockIdx.y;
+  const int x0 = seg * TX;
+  const long long P = (long long)X * Y * Z;
+  const long long base = (long long)b * P;
+  float acc[2][4][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[m][n][e] = 0.f;
+  // ldmatrix lane address: matrix mi = lane/8, row i = lane%8 -> point row
+  // i + 8*(mi & 1), channel offset 8*(mi >> 1)
+  const int mi = lane >> 3, li = lane & 7;
+  const int prow = li + 8 * (mi & 1), coff = 16 * (mi >> 1);
+  for (int ab = 0; ab < 9; ++ab) {
+    if (ab % 3 == 0) {               // stage the three rows (a, b = 0..2) of this z offset
+      const int a = ab / 3;
+      __syncthreads();
+      for (int bb = 0; bb < 3; ++bb) {
+        const long long rowbase = base + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+        load_row(sm + bb * (TX + 2) * ROWB, Hin, rowbase, X, x0, TX, tid, nthr);
+      }
+      __syncthreads();
+    }
+    const unsigned char* rowt = sm + (ab % 3) * (TX + 2) * ROWB;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int tap = ab * 3 + c;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t af[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const int pt = warp * 32 + m * 16 + prow + c;     // row (x + c - 1) in the staged segment
+          ldsm_x4(af[m], rowt + pt * ROWB + ks * 32 + coff);
+        }
+#pragma unroll
+        for (int n = 0; n < 4; ++n) {
+          const uint2 bw = __ldg(Wf + ((tap * 2 + ks) * 4 + n) * 32 + lane);
+          const uint32_t bf[2] = {bw.x, bw.y};
+          mma_bf16(acc[0][n], af[0], bf);
+          mma_bf16(acc[1][n], af[1], bf);
+        }
+      }
+    }
+  }
+  // epilogue: C fragment (row g / g+8, cols 2t, 2t+1)
+  const int g = lane >> 2, t = lane & 3;
+  const long long rowp = base + ((long long)z * Y + y) * X + x0 + warp * 32;
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const long long p = rowp + m * 16 + g + 8 * h;
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        const int co = n * 8 + 2 * t;
+        float v0 = acc[m][n][2 * h], v1 = acc[m][n][2 * h + 1];
+        if (mode == 0) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        } else {
+          const __nv_bfloat162 mk = *reinterpret_cast<const __nv_bfloat162*>(Hmask + p * C + co);
+          v0 = __bfloat162float(mk.x) > 0.f ? v0 : 0.f;
+          v1 = __bfloat162float(mk.y) > 0.f ? v1 : 0.f;
+        }
+        *reinterpret_cast<uint32_t*>(Hout + p * C + co) = pack_bf16(v0, v1);
+      }
+    }
+}
+
+// Weight gradient of a 32 -> 32 layer: dW[tap][ci][co] = sum_p Hin[p + off(tap)][ci] * dZ[p][co].
+// Nine warps per block, warp (a, b) owning the three taps (a, b, c); the block
+// walks rows of its share and writes one float32 partial per tap, ci, co.
+__global__ void __launch_bounds__(288) k_wgrad_mma(const __nv_bfloat16* __restrict__ Hin,
+                                                   const __nv_bfloat16* __restrict__ dZ, float* __restrict__ part,
+                                                   int X, int Y, int Z, int B, int TX) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int segs = X / TX;
+  const long long nrows = (long long)B * Z * Y * segs;
+  unsigned char* dzt = sm + 9 * (TX + 2) * ROWB;
+  float acc[3][2][4][4];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[c][m][n][e] = 0.f;
+  const long long P = (long long)X * Y * Z;
+  const int mi = lane >> 3, li = lane & 7;
+  for (long long rr = blockIdx.x; rr < nrows; rr += gridDim.x) {
+    long long r = rr;
+    const int seg = (int)(r % segs);
+    r /= segs;
+    const int y = (int)(r % Y);
+    r /= Y;
+    const int z = (int)(r % Z);
+    const int b = (int)(r / Z);
+    const int x0 = seg * TX;
+    const long long base = (long long)b * P;
+    __syncthreads();
+    for (int a = 0; a < 3; ++a)
+      for (int bb = 0; bb < 3; ++bb) {
+        const long long rowbase = base + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+        load_row(sm + (a * 3 + bb) * (TX + 2) * ROWB, Hin, rowbase, X, x0, TX, tid, nthr);
+      }
+    {
+      const long long rowbase = base + ((long long)z * Y + y) * X;
+      for (int i = tid; i < TX * 4; i += nthr) {
+        const int pt = i >> 2, q = i & 3;
+        *reinterpret_cast<uint4*>(dzt + pt * ROWB + q * 16) =
+            *reinterpret_cast<const uint4*>(dZ + (rowbase + x0 + pt) * C + q * 8);
+      }
+    }
+    __syncthreads();
+    if (warp < 9) {
+      const unsigned char* rowt = sm + warp * (TX + 2) * ROWB;
+      for (int k0 = 0; k0 < TX; k0 += 16) {
+        // B fragments (k = points, n = co) from dZ: transposed 8x8 loads.
+        // matrices: mi&1 selects k half (points k0..7 / 8..15), mi>>1 selects n tile pair
+        uint32_t bfr[4][2];
+#pragma unroll
+        for (int np = 0; np < 2; ++np) {
+          uint32_t rgs[4];
+          // lane address: rows = points k0 + li + 8*(mi & 1), channels 16*np + 8*(mi >> 1)
+          ldsm_x4_t(rgs, dzt + (k0 + li + 8 * (mi & 1)) * ROWB + (16 * np + 8 * (mi >> 1)) * 2);
+          bfr[2 * np + 0][0] = rgs[0];
+          bfr[2 * np + 0][1] = rgs[1];
+          bfr[2 * np + 1][0] = rgs[2];
+          bfr[2 * np + 1][1] = rgs[3];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          // A fragments (m = ci, k = points) from the shifted input row, transposed loads:
+          // matrices 0: ci 0-7, k 0-7; 1: ci 8-15, k 0-7; 2: ci 0-7, k 8-15; 3: ci 8-15, k 8-15
+#pragma unroll
+          for (int m = 0; m < 2; ++m) {
+            uint32_t af[4];
+            const int kk = k0 + li + 8 * (mi >> 1);
+            const int cc = m * 16 + 8 * (mi & 1);
+            ldsm_x4_t(af, rowt + (kk + c) * ROWB + cc * 2);
+#pragma unroll
+            for (int n = 0; n < 4; ++n) mma_bf16(acc[c][m][n], af, bfr[n]);
+          }
+        }
+      }
+    }
+  }
+  if (warp < 9) {
+    const int g = lane >> 2, t = lane & 3;
+    float* pb = part + (long long)blockIdx.x * TAPS * C * C;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int tap = warp * 3 + c;
+#pragma unroll
+      for (int m = 0; m < 2; ++m)
+#pragma unroll
+        for (int n = 0; n < 4; ++n)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int ci = m * 16 + g + 8 * (e >> 1), co = n * 8 + 2 * t + (e & 1);
+            pb[(tap * C + ci) * C + co] = acc[c][m][n][e];
+          }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA-core layers and helpers.
+
+// Packs float32 weights W[tap][ci][co] into mma B fragments:
+// Wf[((tap*2 + ks)*4 + n)*32 + lane] = {B(2t, g), B(2t+1, g)}, {B(2t+8, g), B(2t+9, g)}
+// with k = 16 ks + row, n8 tile n, g = lane/4, t = lane%4, B(k, j) = W[tap][k][8n + j];
+// transposed: B(k, j) = W[26 - tap][8n + j][k] (backward data: flipped taps, swapped channels).
+__global__ void k_pack_frag(const float* __restrict__ W, uint2* __restrict__ Wf, int transposed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= TAPS * 2 * 4 * 32) return;
+  const int lane = i & 31, n = (i >> 5) & 3, ks = (i >> 7) & 1, tap = i >> 8;
+  const int g = lane >> 2, t = lane & 3;
+  auto Bv = [&](int k, int j) {
+    const int kk = ks * 16 + k, jj = n * 8 + j;
+    return transposed ? W[((TAPS - 1 - tap) * C + jj) * C + kk] : W[(tap * C + kk) * C + jj];
+  };
+  Wf[i] = make_uint2(pack_bf16(Bv(2 * t, g), Bv(2 * t + 1, g)), pack_bf16(Bv(2 * t + 8, g), Bv(2 * t + 9, g)));
+}
+
+// sum of squares of each sample (float64 partials per block, then per sample)
+__global__ void k_sumsq(const float* __restrict__ u, long long P, double* __restrict__ out) {
+  const int b = blockIdx.y;
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+    const double v = u[(long long)b * P + i];
+    s += v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    atomicAdd(out + b, t);
+  }
+}
+
+// Layer 1: H1[p][co] = relu(sum_tap W1[tap][co] * x0[p + off(tap)]), x0 = u_bar / sigma.
+__global__ void __launch_bounds__(256) k_conv_in(const float* __restrict__ ubar, const double* __restrict__ sumsq,
+                                                 const float* __restrict__ W1, __nv_bfloat16* __restrict__ H1,
+                                                 int X, int Y, int Z) {
+  const long long P = (long long)X * Y * Z;
+  const int b = blockIdx.y;
+  __shared__ float w[TAPS * C];
+  for (int i = threadIdx.x; i < TAPS * C; i += blockDim.x) w[i] = W1[i];
+  __syncthreads();
+  const float inv_sigma = (float)(1.0 / sqrt(fmax(sumsq[b] / (double)P, 1e-300)));
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
+    float in[TAPS];
+    for (int a = 0; a < 3; ++a)
+      for (int bb = 0; bb < 3; ++bb) {
+        const long long row = (long long)b * P + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+        for (int c = 0; c < 3; ++c) in[(a * 3 + bb) * 3 + c] = ubar[row + wrap(x + c - 1, X)] * inv_sigma;
+      }
+    uint4* dst = reinterpret_cast<uint4*>(H1 + ((long long)b * P + p) * C);
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      uint32_t ow[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int co = q * 8 + 2 * k;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int t = 0; t < TAPS; ++t) {
+          s0 = fmaf(w[t * C + co], in[t], s0);
+          s1 = fmaf(w[t * C + co + 1], in[t], s1);
+        }
+        ow[k] = pack_bf16(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
+      }
+      dst[q] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    }
+  }
+}
+
+// Layer 4 and the residual output: u0 = u_bar + sigma * A * sum_{tap, ci} W4[tap][ci] H3[p + off][ci].
+// With utrue != nullptr it also writes g = sigma * A * 2 (u0 - u_true) / ||u_true||^2 / B (the
+// gradient of the batch-mean loss with respect to the layer-4 output) and accumulates
+// sum (u0 - u_true)^2 / ||u_true||^2 / B into loss.
+__global__ void __launch_bounds__(256) k_conv_out(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ W4,
+                                                  const float* __restrict__ ubar, const double* __restrict__ sumsq,
+                                                  float* __restrict__ u0, const float* __restrict__ utrue,
+                                                  const double* __restrict__ tsumsq, float* __restrict__ gout,
+                                                  double* __restrict__ loss, int X, int Y, int Z, int B,
+                                                  double ascale) {
+  const long long P = (long long)X * Y * Z;
+  const int b = blockIdx.y;
+  __shared__ float w[TAPS * C];
+  for (int i = threadIdx.x; i < TAPS * C; i += blockDim.x) w[i] = W4[i];
+  __syncthreads();
+  const double sigma = sqrt(fmax(sumsq[b] / (double)P, 1e-300)) * ascale;   // sigma * A
+  double lsum = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
+    float s = 0.f;
+    for (int a = 0; a < 3; ++a)
+      for (int bb = 0; bb < 3; ++bb) {
+        const long long row = (long long)b * P + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+        for (int c = 0; c < 3; ++c) {
+          const int t = (a * 3 + bb) * 3 + c;
+          const uint4* src = reinterpret_cast<const uint4*>(H3 + (row + wrap(x + c - 1, X)) * C);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const uint4 v = src[q];
+            const uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&wds[k]);
+              const int ci = q * 8 + 2 * k;
+              s = fmaf(w[t * C + ci], __bfloat162float(h.x), s);
+              s = fmaf(w[t * C + ci + 1], __bfloat162float(h.y), s);
+            }
+          }
+        }
+      }
+    const long long gi = (long long)b * P + p;
+    const float uo = ubar[gi] + (float)sigma * s;
+    u0[gi] = uo;
+    if (utrue) {
+      const double d = (double)uo - (double)utrue[gi];
+      const double inv = 1.0 / (tsumsq[b] * (double)B);
+      lsum += d * d * inv;
+      gout[gi] = (float)(sigma * 2.0 * d * inv);
+    }
+  }
+  if (utrue) {
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    __shared__ double red[32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[w2];
+      atomicAdd(loss, t);
+    }
+  }
+}
+
+// Layer-4 backward data with the layer-3 ReLU mask:
+// dZ3[p][ci] = (H3[p][ci] > 0) * sum_tap W4[tap][ci] * g[p - off(tap)].
+__global__ void __launch_bounds__(256) k_conv_out_bwd(const float* __restrict__ g, const float* __restrict__ W4,
+                                                      const __nv_bfloat16* __restrict__ H3,
+                                                      __nv_bfloat16* __restrict__ dZ3, int X, int Y, int Z) {
+  const long long P = (long long)X * Y * Z;
+  const int b = blockIdx.y;
+  __shared__ float w[TAPS * C];
+  for (int i = threadIdx.x; i < TAPS * C; i += blockDim.x) w[i] = W4[i];
+  __syncthreads();
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
+    float gv[TAPS];
+    for (int a = 0; a < 3; ++a)
+      for (int bb = 0; bb < 3; ++bb) {
+        const long long row = (long long)b * P + ((long long)wrap(z - a + 1, Z) * Y + wrap(y - bb + 1, Y)) * X;
+        for (int c = 0; c < 3; ++c) gv[(a * 3 + bb) * 3 + c] = g[row + wrap(x - c + 1, X)];
+      }
+    const long long gi = (long long)b * P + p;
+    const uint4* hm = reinterpret_cast<const uint4*>(H3 + gi * C);
+    uint4* dst = reinterpret_cast<uint4*>(dZ3 + gi * C);
+#pragma unroll 1
+    for (int q = 0; q < 4; ++q) {
+      const uint4 mv = hm[q];
+      const uint32_t mw[4] = {mv.x, mv.y, mv.z, mv.w};
+      uint32_t ow[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int ci = q * 8 + 2 * k;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int t = 0; t < TAPS; ++t) {
+          s0 = fmaf(w[t * C + ci], gv[t], s0);
+          s1 = fmaf(w[t * C + ci + 1], gv[t], s1);
+        }
+        const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[k]);
+        ow[k] = pack_bf16(__bfloat162float(m2.x) > 0.f ? s0 : 0.f, __bfloat162float(m2.y) > 0.f ? s1 : 0.f);
+      }
+      dst[q] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+    }
+  }
+}
+
+// Weight gradients of the 1-channel layers (float32 partials per block):
+//   first (layer 1): part[tap][co] = sum_p x0[p + off(tap)] * dZ1[p][co]
+//   last  (layer 4): part[tap][ci] = sum_p H3[p + off(tap)][ci] * g[p]
+// One thread per (point, channel) pair keeps 27 running sums.
+__global__ void __launch_bounds__(256) k_wgrad_small(const float* __restrict__ ubar, const double* __restrict__ sumsq,
+                                                     const __nv_bfloat16* __restrict__ dZ1,
+                                                     const __nv_bfloat16* __restrict__ H3, const float* __restrict__ g,
+                                                     float* __restrict__ part, int X, int Y, int Z, int B, int last) {
+  const long long P = (long long)X * Y * Z;
+  const int ch = threadIdx.x & 31;
+  const int lanes = (blockDim.x >> 5) * gridDim.x;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  float acc[TAPS];
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t) acc[t] = 0.f;
+  for (long long q = slot; q < (long long)B * P; q += lanes) {
+    const int b = (int)(q / P);
+    const long long p = q - (long long)b * P;
+    const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
+    const float fac = last ? g[q] : __bfloat162float(dZ1[q * C + ch]);
+    const float inv_sigma = last ? 1.f : (float)(1.0 / sqrt(fmax(sumsq[b] / (double)P, 1e-300)));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        const long long row = (long long)b * P + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const long long src = row + wrap(x + c - 1, X);
+          const float v = last ? __bfloat162float(H3[src * C + ch]) : ubar[src] * inv_sigma;
+          acc[(a * 3 + bb) * 3 + c] = fmaf(v, fac, acc[(a * 3 + bb) * 3 + c]);
+        }
+      }
+  }
+  float* pb = part + (long long)slot * TAPS * C;
+#pragma unroll
+  for (int t = 0; t < TAPS; ++t) pb[t * C + ch] = acc[t];
+}
+
+// out[i] = sum_j part[j][i] (fixed order), j < nparts, i < n.
+__global__ void k_reduce_parts(const float* __restrict__ part, int nparts, int n, float* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double s = 0.0;
+  for (int j = 0; j < nparts; ++j) s += part[(long long)j * n + i];
+  out[i] = (float)s;
+}
+
+// Adam on the float32 master weights.
+__global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                       const float* __restrict__ grad, int n, float lr, float b1, float b2, float eps, float c1,
+                       float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = grad[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// ---------------------------------------------------------------------------
+// Host drivers (called by the C ABI in api.cu).
+
+int cnn_tile(int X) { return X % 64 == 0 ? 64 : 32; }
+
+size_t cnn_conv_smem(int X) { return (size_t)3 * (cnn_tile(X) + 2) * ROWB; }
+
+bool cnn_shape_ok(int X, int Y, int Z) { return X % 32 == 0 && Y >= 3 && Z >= 3; }
+
+cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const float* utrue, int X, int Y, int Z,
+                        int B, double ascale, cudaStream_t s) {
+  const long long P = (long long)X * Y * Z;
+  const int TX = cnn_tile(X);
+  const size_t sm = cnn_conv_smem(X);
+  cudaError_t e = cudaMemsetAsync(w.sumsq, 0, sizeof(double) * 2 * B + sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  const dim3 gp((unsigned)((P + 255) / 256 < 2048 ? (P + 255) / 256 : 2048), B);
+  k_sumsq<<<gp, 256, 0, s>>>(ubar, P, w.sumsq);
+  if (utrue) k_sumsq<<<gp, 256, 0, s>>>(utrue, P, w.sumsq + B);
+  k_conv_in<<<gp, 256, 0, s>>>(ubar, w.sumsq, w.master, w.H1, X, Y, Z);
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_conv_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  const dim3 gc((unsigned)(X / TX) * Y * Z, B);
+  k_conv_mma<<<gc, TX, sm, s>>>(w.H1, w.frag2, w.H2, nullptr, X, Y, Z, TX, 0);
+  k_conv_mma<<<gc, TX, sm, s>>>(w.H2, w.frag3, w.H3, nullptr, X, Y, Z, TX, 0);
+  k_conv_out<<<gp, 256, 0, s>>>(w.H3, w.master + kW4, ubar, w.sumsq, u0, utrue, w.sumsq + B, w.g, w.sumsq + 2 * B,
+                                X, Y, Z, B, ascale);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s) {
+  const int n = TAPS * 2 * 4 * 32;
+  k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW2, w.frag2, 0);
+  k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW3, w.frag3, 0);
+  k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW2, w.frag2t, 1);
+  k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW3, w.frag3t, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, int Z, int B, cudaStream_t s) {
+  const long long P = (long long)X * Y * Z;
+  const int TX = cnn_tile(X);
+  const size_t sm = cnn_conv_smem(X);
+  const dim3 gp((unsigned)((P + 255) / 256 < 2048 ? (P + 255) / 256 : 2048), B);
+  const dim3 gc((unsigned)(X / TX) * Y * Z, B);
+  // layer 4
+  k_conv_out_bwd<<<gp, 256, 0, s>>>(w.g, w.master + kW4, w.H3, w.dA, X, Y, Z);
+  k_wgrad_small<<<kSmallBlocks, 256, 0, s>>>(ubar, w.sumsq, nullptr, w.H3, w.g, w.part, X, Y, Z, B, 1);
+  k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks * 8, TAPS * C, w.grad + kW4);
+  // layer 3: dW3 from (H2, dZ3); dZ2 = conv^T(dZ3, W3) masked by H2
+  const size_t smw = (size_t)10 * (TX + 2) * ROWB;
+  cudaError_t e = cudaFuncSetAttribute(k_wgrad_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
+  if (e != cudaSuccess) return e;
+  k_wgrad_mma<<<kWgradBlocks, 288, smw, s>>>(w.H2, w.dA, w.part, X, Y, Z, B, TX);
+  k_reduce_parts<<<(TAPS * C * C + 255) / 256, 256, 0, s>>>(w.part, kWgradBlocks, TAPS * C * C, w.grad + kW3);
+  k_conv_mma<<<gc, TX, sm, s>>>(w.dA, w.frag3t, w.dB, w.H2, X, Y, Z, TX, 1);
+  // layer 2: dW2 from (H1, dZ2); dZ1 = conv^T(dZ2, W2) masked by H1
+  k_wgrad_mma<<<kWgradBlocks, 288, smw, s>>>(w.H1, w.dB, w.part, X, Y, Z, B, TX);
+  k_reduce_parts<<<(TAPS * C * C + 255) / 256, 256, 0, s>>>(w.part, kWgradBlocks, TAPS * C * C, w.grad + kW2);
+  k_conv_mma<<<gc, TX, sm, s>>>(w.dB, w.frag2t, w.dA, w.H1, X, Y, Z, TX, 1);
+  // layer 1
+  k_wgrad_small<<<kSmallBlocks, 256, 0, s>>>(ubar, w.sumsq, w.dA, nullptr, nullptr, w.part, X, Y, Z, B, 0);
+  k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks * 8, TAPS * C, w.grad + kW1);
+  return cudaGetLastError();
+}
+
+cudaError_t cnn_adam(const CnnBuffers& w, int step, float lr, cudaStream_t s) {
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  k_adam<<<(kCnnWeights + 255) / 256, 256, 0, s>>>(w.master, w.m, w.v, w.grad, kCnnWeights, lr, b1, b2, 1e-8f, c1, c2);
+  return cudaGetLastError();
+}
+
+}  // namespace gad

@@ -1,0 +1,52 @@
+// Buffers and host drivers of the learned-guess network (cnn.cu).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gad {
+
+// float32 master weight layout (see cnn.cu)
+constexpr int kW1 = 0;                       // [27][32]
+constexpr int kW2 = kW1 + 27 * 32;           // [27][32][32]
+constexpr int kW3 = kW2 + 27 * 32 * 32;      // [27][32][32]
+constexpr int kW4 = kW3 + 27 * 32 * 32;      // [27][32]
+constexpr int kCnnWeights = kW4 + 27 * 32;
+constexpr int kSmallBlocks = 152;            // blocks of the 1-channel weight-gradient kernel (8 warps each)
+constexpr int kWgradBlocks = 304;            // blocks of the 32x32 weight-gradient kernel
+
+struct CnnBuffers {
+  float* master = nullptr;     // weights
+  float* m = nullptr;          // Adam moments
+  float* v = nullptr;
+  float* grad = nullptr;
+  uint2* frag2 = nullptr;      // layer 2/3 weights in mma fragment order (forward)
+  uint2* frag3 = nullptr;
+  uint2* frag2t = nullptr;     // flipped, channel-swapped (backward data)
+  uint2* frag3t = nullptr;
+  __nv_bfloat16* H1 = nullptr; // activations [B][P][32]
+  __nv_bfloat16* H2 = nullptr;
+  __nv_bfloat16* H3 = nullptr;
+  __nv_bfloat16* dA = nullptr; // gradient scratch [B][P][32]
+  __nv_bfloat16* dB = nullptr;
+  float* g = nullptr;          // dL/dy of the last layer [B][P]
+  double* sumsq = nullptr;     // [B] sum u_bar^2, [B] sum u_true^2, [1] loss
+  float* part = nullptr;       // weight-gradient partials
+};
+
+// floats of the weight-gradient partial buffer
+constexpr long long kCnnPartFloats = (long long)kWgradBlocks * 27 * 32 * 32 > (long long)kSmallBlocks * 8 * 27 * 32
+                                         ? (long long)kWgradBlocks * 27 * 32 * 32
+                                         : (long long)kSmallBlocks * 8 * 27 * 32;
+
+bool cnn_shape_ok(int X, int Y, int Z);
+cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s);
+// ascale = A = 1/(pi gamma)^2, the fixed output scale
+cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const float* utrue, int X, int Y, int Z,
+                        int B, double ascale, cudaStream_t s);
+cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, int Z, int B, cudaStream_t s);
+cudaError_t cnn_adam(const CnnBuffers& w, int step, float lr, cudaStream_t s);
+
+}  // namespace gad
