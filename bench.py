@@ -235,7 +235,82 @@ def _extra_workloads(gad, dev, extras):
                                "shape_groups": len(groups), "iterations_mean": float(np.mean(its)),
                                "converged": bool(np.all(res[2] == gad.AD_OK)), "launches": launches,
                                "one_call_per_group_mpoints_s": pts / t_seq / 1e6}
+    if "learned512" in extras:
+        out["velocity3d_512_f32_learned"] = _learned_512(gad, dev)
     return out
+
+
+def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr=1e-4):
+    """Learned initial guess against plain BiCGSTAB on a 512^3 x 3 velocity
+    (gamma = 0.01, tolerance 1e-6, the residual normalised by ||u_bar - G u_bar||
+    for both starts). The network is trained first, on the GPU, on `npairs`
+    pairs (u_true, G u_true) of 64^3 fields drawn with the 512^3 field's
+    spectrum in grid units (wavenumbers scaled by 512/64: the network is local,
+    so it sees the same neighbourhood statistics) and filtered with the same
+    grid-unit filter (gamma = 0.01). Learned wall time = inference + solve."""
+    import torch
+    from synth import fields
+    wl = fields.WORKLOADS["velocity3d_512_f32"]
+    gamma, spec = wl["gamma"], wl["spectrum"]
+    t_gen = time.perf_counter()
+    v = fields.random_velocity_field_torch((n,) * 3, 0, spec, device=dev)
+    ub = gad.filter(v, gamma, ndim=3)
+    del v
+    spec_t = lambda k: spec(np.asarray(k) * (n / n_train))
+    ut = torch.empty((npairs,) + (n_train,) * 3, device=dev)
+    for i in range(0, npairs, 3):
+        m = min(3, npairs - i)
+        ut[i:i + m] = fields.random_velocity_field_torch((n_train,) * 3, 10_000 + i, spec_t, device=dev)[:m]
+    ubt = gad.filter(ut, gamma, ndim=3)
+    torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
+    w = gad.guess_init(seed=1, stencil=True)
+    w_stencil = w.clone()
+    gad.guess_train(w.clone(), ubt[:batch], ut[:batch], gamma, epochs=1, batch=batch, lr=lr, seed=0)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = gad.guess_train(w, ubt, ut, gamma, epochs=epochs, batch=batch, lr=lr, seed=3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    del ut, ubt
+    torch.cuda.empty_cache()
+
+    def solve(u0=None):
+        return gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=4000, ndim=3, u0=u0, history=False)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=2, ndim=3, history=False)     # plans, graph
+    gad.guess_infer(w, ub, gamma)
+    plain, t_plain = timed(solve)
+    u0, t_inf = timed(lambda: gad.guess_infer(w, ub, gamma))
+    learned, t_solve = timed(lambda: solve(u0))
+    u0s = gad.guess_infer(w_stencil, ub, gamma)
+    stencil, t_stencil = timed(lambda: solve(u0s))
+    diff = float(torch.linalg.vector_norm(learned.u - plain.u) / torch.linalg.vector_norm(plain.u))
+    pts = 3.0 * n ** 3
+    t_learned = t_inf + t_solve
+    return {
+        "shape": [n] * 3, "components": 3, "gamma": gamma, "tol": 1e-6,
+        "plain": {"ms": t_plain * 1e3, "mpoints_s": pts / t_plain / 1e6,
+                  "iterations": [int(x) for x in plain.iterations],
+                  "converged": bool(np.all(plain.status == gad.AD_OK))},
+        "learned": {"ms": t_learned * 1e3, "infer_ms": t_inf * 1e3, "solve_ms": t_solve * 1e3,
+                    "mpoints_s": pts / t_learned / 1e6, "iterations": [int(x) for x in learned.iterations],
+                    "converged": bool(np.all(learned.status == gad.AD_OK))},
+        "stencil_start_untrained": {"solve_ms": t_stencil * 1e3,
+                                    "iterations": [int(x) for x in stencil.iterations]},
+        "wall_time_ratio_plain_over_learned": t_plain / t_learned,
+        "rel_l2_learned_vs_plain_solution": diff,
+        "train": {"pairs": npairs, "shape": [n_train] * 3, "epochs": epochs, "batch": batch, "lr": lr,
+                  "seconds": t_train, "loss_per_epoch": [float(x) for x in hist],
+                  "data_generation_s": t_gen, "init": "explicit-inverse stencil"},
+    }
 
 
 def run_reference(args):
@@ -284,8 +359,8 @@ def main():
                     help="drive the iteration loop from the host instead of a graph while node (same kernels; "
                          "profilers cannot see kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="fields per GPU")
-    ap.add_argument("--extras", default="methods,3d256,uneven48",
-                    help="comma list of extra measurements on rank 0: methods, 3d256, uneven48")
+    ap.add_argument("--extras", default="methods,3d256,uneven48,learned512",
+                    help="comma list of extra measurements on rank 0: methods, 3d256, uneven48, learned512")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -448,7 +523,7 @@ def main():
                                            "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
                                            "extrapolated to the %d passes the GPU solve of that field needed"
                                            % (args.method, t0, sample_passes, per, n0))}
-    if rank == 0 and (extras & {"3d256", "uneven48"}):
+    if rank == 0 and (extras & {"3d256", "uneven48", "learned512"}):
         del out, dev_in, host_out
         torch.cuda.empty_cache()
         line["workloads"] = _extra_workloads(gad, dev, extras)

@@ -23,7 +23,8 @@
  *     (float for AD_F32, double for AD_F64). The library owns its workspace
  *     (spectral buffers, Krylov vectors, scalars) inside the context and
  *     allocates it on the first call for a grid shape and batch size; later
- *     calls with that shape allocate nothing.
+ *     calls with that shape allocate nothing. A call takes at most
+ *     AD_MAX_BATCH fields (each field owns one row of the launch grid).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream). Work is enqueued on it.
  *   - No entry point throws. Arguments are checked before any launch; an
@@ -34,6 +35,8 @@
 #define GAD_H
 
 #include <stdint.h>
+
+#define AD_MAX_BATCH 65535
 
 #ifdef __cplusplus
 extern "C" {

@@ -312,6 +312,7 @@ void free_plan(Plan* p) {
 }
 
 ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
+  if (batch > AD_MAX_BATCH) return fail(ctx, AD_ERR_ARG, "batch > AD_MAX_BATCH");
   const std::string key = plan_key(g, batch);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) { *out = it->second; return AD_OK; }
@@ -836,6 +837,7 @@ ad_status cnn_alloc(ad_ctx* ctx, CnnWork* cw, void** out, size_t bytes) {
 
 // Workspace for (X, Y, Z, B); `training` adds gradients, moments and gathers.
 ad_status get_cnn(ad_ctx* ctx, const ad_grid* g, int B, bool training, CnnWork** out) {
+  if (B > AD_MAX_BATCH) return fail(ctx, AD_ERR_ARG, "batch > AD_MAX_BATCH");
   char key[128];
   snprintf(key, sizeof key, "%lld:%lld:%lld:%d", (long long)g->n[0], (long long)g->n[1], (long long)g->n[2], B);
   auto it = ctx->cnn.find(key);

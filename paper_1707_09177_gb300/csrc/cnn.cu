@@ -457,43 +457,101 @@ __global__ void __launch_bounds__(256) k_conv_out_bwd(const float* __restrict__ 
   }
 }
 
-// Weight gradients of the 1-channel layers (float32 partials per block):
-//   first (layer 1): part[tap][co] = sum_p x0[p + off(tap)] * dZ1[p][co]
-//   last  (layer 4): part[tap][ci] = sum_p H3[p + off(tap)][ci] * g[p]
-// One thread per (point, channel) pair keeps 27 running sums.
-__global__ void __launch_bounds__(256) k_wgrad_small(const float* __restrict__ ubar, const double* __restrict__ sumsq,
-                                                     const __nv_bfloat16* __restrict__ dZ1,
-                                                     const __nv_bfloat16* __restrict__ H3, const float* __restrict__ g,
-                                                     float* __restrict__ part, int X, int Y, int Z, int B, int last) {
+// Weight gradients of the 1-channel layers, as one correlation of a scalar
+// field S with a 32-channel field V:
+//   acc[tap][ch] = sum_p S[p + off(tap)] * scale_b * V[p][ch]
+//   first (layer 1): S = u_bar, scale_b = 1/sigma_b, V = dZ1 -> dW1[tap][co]
+//   last  (layer 4): S = g, scale_b = 1, V = H3; dW4[tap][ci] = sum_p H3[p + off(tap)][ci] g[p]
+//                    = sum_q H3[q][ci] g[q - off(tap)], stored at the mirrored tap 26 - tap.
+// A block walks segments (b, z, y, x0..x0+TW) of its share; the 3x3 neighbour
+// rows of S over [x0 - 1, x0 + TW + 1) are staged in shared memory with
+// cp.async one segment ahead (double buffer). Warp w owns TW/8 consecutive
+// points and lane = channel: the three x taps of consecutive points share a
+// sliding register window, so each point costs 9 shared loads, one 64-byte
+// coalesced load of V and 27 FMAs per lane. The warps' sums are added in the
+// block (fixed order) and written as one float32 partial of 27 x 32 per block.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Stages the 9 neighbour rows of S for segment r (see k_wgrad_1ch).
+__device__ __forceinline__ void stage_1ch(float* dst, const float* __restrict__ S, long long r, int segs, int X,
+                                          int Y, int Z, int TW, long long P) {
+  const int seg = (int)(r % segs);
+  long long q = r / segs;
+  const int y = (int)(q % Y);
+  q /= Y;
+  const int z = (int)(q % Z), b = (int)(q / Z);
+  const int x0 = seg * TW, ld = TW + 2;
+  for (int i = threadIdx.x; i < 9 * ld; i += blockDim.x) {
+    const int rr = i / ld, j = i - rr * ld;
+    const long long src = (long long)b * P + ((long long)wrap(z + rr / 3 - 1, Z) * Y + wrap(y + rr % 3 - 1, Y)) * X +
+                          wrap(x0 - 1 + j, X);
+    cp_async4(dst + i, S + src);
+  }
+}
+
+__global__ void __launch_bounds__(256, 3) k_wgrad_1ch(const float* __restrict__ S, const double* __restrict__ sumsq,
+                                                   const __nv_bfloat16* __restrict__ V, float* __restrict__ part,
+                                                   int X, int Y, int Z, int B, int TW, int mirror) {
+  extern __shared__ __align__(16) float sw[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const long long P = (long long)X * Y * Z;
-  const int ch = threadIdx.x & 31;
-  const int lanes = (blockDim.x >> 5) * gridDim.x;
-  const int slot = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int segs = X / TW, ld = TW + 2, nst = 9 * ld;
+  const long long nrows = (long long)B * Z * Y * segs;
   float acc[TAPS];
 #pragma unroll
   for (int t = 0; t < TAPS; ++t) acc[t] = 0.f;
-  for (long long q = slot; q < (long long)B * P; q += lanes) {
-    const int b = (int)(q / P);
-    const long long p = q - (long long)b * P;
-    const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
-    const float fac = last ? g[q] : __bfloat162float(dZ1[q * C + ch]);
-    const float inv_sigma = last ? 1.f : (float)(1.0 / sqrt(fmax(sumsq[b] / (double)P, 1e-300)));
+  const int npw = TW / 8, xs = warp * npw;
+  long long r = blockIdx.x;
+  if (r < nrows) stage_1ch(sw, S, r, segs, X, Y, Z, TW, P);
+  cp_async_commit();
+  for (int it = 0; r < nrows; ++it, r += gridDim.x) {
+    if (r + gridDim.x < nrows) stage_1ch(sw + ((it + 1) & 1) * nst, S, r + gridDim.x, segs, X, Y, Z, TW, P);
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    const float* sb = sw + (it & 1) * nst;
+    const int seg = (int)(r % segs);
+    const long long q = r / segs;                   // (b, z, y) row index
+    const int b = (int)(q / ((long long)Z * Y));
+    const float scale = sumsq ? (float)(1.0 / sqrt(fmax(sumsq[b] / (double)P, 1e-300))) : 1.f;
+    const __nv_bfloat16* vrow = V + (q * X + seg * TW + xs) * C + lane;
+    float win[9][3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
+    for (int k = 0; k < 9; ++k) {
+      win[k][0] = sb[k * ld + xs];
+      win[k][1] = sb[k * ld + xs + 1];
+    }
+#pragma unroll 4
+    for (int i = 0; i < npw; ++i) {
+      const float v = __bfloat162float(vrow[(long long)i * C]) * scale;
 #pragma unroll
-      for (int bb = 0; bb < 3; ++bb) {
-        const long long row = (long long)b * P + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+      for (int k = 0; k < 9; ++k) {
+        win[k][2] = sb[k * ld + xs + i + 2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const long long src = row + wrap(x + c - 1, X);
-          const float v = last ? __bfloat162float(H3[src * C + ch]) : ubar[src] * inv_sigma;
-          acc[(a * 3 + bb) * 3 + c] = fmaf(v, fac, acc[(a * 3 + bb) * 3 + c]);
-        }
+        for (int c = 0; c < 3; ++c) acc[k * 3 + c] = fmaf(win[k][c], v, acc[k * 3 + c]);
+        win[k][0] = win[k][1];
+        win[k][1] = win[k][2];
       }
+    }
+    __syncthreads();
   }
-  float* pb = part + (long long)slot * TAPS * C;
+  // block sum of the warps' partials, fixed order
+  float* red = sw;
 #pragma unroll
-  for (int t = 0; t < TAPS; ++t) pb[t * C + ch] = acc[t];
+  for (int t = 0; t < TAPS; ++t) red[(warp * TAPS + t) * C + lane] = acc[t];
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  for (int i = tid; i < TAPS * C; i += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < nw; ++w) s += red[w * TAPS * C + i];
+    const int tap = i / C, ch = i - tap * C;
+    part[(long long)blockIdx.x * TAPS * C + (mirror ? TAPS - 1 - tap : tap) * C + ch] = s;
+  }
 }
 
 // out[i] = sum_j part[j][i] (fixed order), j < nparts, i < n.
@@ -560,6 +618,19 @@ cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// x-segment of the 1-channel weight-gradient kernel: X itself up to 256 points,
+// else the largest multiple of 32 up to 256 that divides X (X is a multiple of 32)
+static int wgrad_1ch_tile(int X) {
+  if (X <= 256) return X;
+  for (int t = 256; t > 32; t -= 32)
+    if (X % t == 0) return t;
+  return 32;
+}
+static size_t wgrad_1ch_smem(int TW) {
+  const size_t stage = sizeof(float) * 2 * 9 * (TW + 2), red = sizeof(float) * 8 * TAPS * C;
+  return stage > red ? stage : red;
+}
+
 cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, int Z, int B, cudaStream_t s) {
   const long long P = (long long)X * Y * Z;
   const int TX = cnn_tile(X);
@@ -568,8 +639,10 @@ cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, i
   const dim3 gc((unsigned)(X / TX) * Y * Z, B);
   // layer 4
   k_conv_out_bwd<<<gp, 256, 0, s>>>(w.g, w.master + kW4, w.H3, w.dA, X, Y, Z);
-  k_wgrad_small<<<kSmallBlocks, 256, 0, s>>>(ubar, w.sumsq, nullptr, w.H3, w.g, w.part, X, Y, Z, B, 1);
-  k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks * 8, TAPS * C, w.grad + kW4);
+  const int TW = wgrad_1ch_tile(X);
+  const size_t sm1 = wgrad_1ch_smem(TW);
+  k_wgrad_1ch<<<kSmallBlocks, 256, sm1, s>>>(w.g, nullptr, w.H3, w.part, X, Y, Z, B, TW, 1);
+  k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks, TAPS * C, w.grad + kW4);
   // layer 3: dW3 from (H2, dZ3); dZ2 = conv^T(dZ3, W3) masked by H2
   const size_t smw = (size_t)10 * (TX + 2) * ROWB;
   cudaError_t e = cudaFuncSetAttribute(k_wgrad_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smw);
@@ -582,8 +655,8 @@ cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, i
   k_reduce_parts<<<(TAPS * C * C + 255) / 256, 256, 0, s>>>(w.part, kWgradBlocks, TAPS * C * C, w.grad + kW2);
   k_conv_mma<<<gc, TX, sm, s>>>(w.dB, w.frag2t, w.dA, w.H1, X, Y, Z, TX, 1);
   // layer 1
-  k_wgrad_small<<<kSmallBlocks, 256, 0, s>>>(ubar, w.sumsq, w.dA, nullptr, nullptr, w.part, X, Y, Z, B, 0);
-  k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks * 8, TAPS * C, w.grad + kW1);
+  k_wgrad_1ch<<<kSmallBlocks, 256, sm1, s>>>(ubar, w.sumsq, w.dA, w.part, X, Y, Z, B, TW, 0);
+  k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks, TAPS * C, w.grad + kW1);
   return cudaGetLastError();
 }
 

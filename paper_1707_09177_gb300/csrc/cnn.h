@@ -14,7 +14,7 @@ constexpr int kW2 = kW1 + 27 * 32;           // [27][32][32]
 constexpr int kW3 = kW2 + 27 * 32 * 32;      // [27][32][32]
 constexpr int kW4 = kW3 + 27 * 32 * 32;      // [27][32]
 constexpr int kCnnWeights = kW4 + 27 * 32;
-constexpr int kSmallBlocks = 152;            // blocks of the 1-channel weight-gradient kernel (8 warps each)
+constexpr int kSmallBlocks = 456;            // blocks of the 1-channel weight-gradient kernel (3 per SM)
 constexpr int kWgradBlocks = 304;            // blocks of the 32x32 weight-gradient kernel
 
 struct CnnBuffers {
@@ -37,9 +37,9 @@ struct CnnBuffers {
 };
 
 // floats of the weight-gradient partial buffer
-constexpr long long kCnnPartFloats = (long long)kWgradBlocks * 27 * 32 * 32 > (long long)kSmallBlocks * 8 * 27 * 32
+constexpr long long kCnnPartFloats = (long long)kWgradBlocks * 27 * 32 * 32 > (long long)kSmallBlocks * 27 * 32
                                          ? (long long)kWgradBlocks * 27 * 32 * 32
-                                         : (long long)kSmallBlocks * 8 * 27 * 32;
+                                         : (long long)kSmallBlocks * 27 * 32;
 
 bool cnn_shape_ok(int X, int Y, int Z);
 cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s);

@@ -231,7 +231,7 @@ ad_status run_static(const ad_grid* g, const void* in, void* out, int batch, cud
 
 extern "C" ad_status ad_filter_static(const ad_grid* grid, const void* in, void* out, int batch, void* stream) {
   if (!grid || (grid->ndim != 2 && grid->ndim != 3) || (grid->dtype != AD_F32 && grid->dtype != AD_F64) ||
-      !(grid->gamma > 0.0) || !std::isfinite(grid->gamma) || batch < 0)
+      !(grid->gamma > 0.0) || !std::isfinite(grid->gamma) || batch < 0 || batch > AD_MAX_BATCH)
     return AD_ERR_ARG;
   for (int d = 0; d < grid->ndim; ++d) {
     const long long n = grid->n[d];

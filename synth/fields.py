@@ -206,3 +206,39 @@ def random_scalar_field_torch(shape, seed, spectrum, device="cuda"):
     u = torch.fft.irfftn(torch.fft.rfftn(w) * amp, s=shape)
     u = u - u.mean()
     return (u / torch.sqrt(torch.mean(u * u))).float()
+
+
+def random_velocity_field_torch(shape, seed, spectrum, device="cuda"):
+    """The recipe of random_velocity_field (three white-noise components shaped
+    to the shell spectrum, Leray projection, Nyquist planes zeroed, joint unit
+    RMS) evaluated with torch on a device; float32 result (3, Nz, Ny, Nx).
+    Seeded by a torch generator, so it differs from the NumPy field."""
+    import torch
+    shape = tuple(int(n) for n in shape)
+    assert len(shape) == 3
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    f64 = dict(device=device, dtype=torch.float64)
+    kz = torch.fft.fftfreq(shape[0], d=1.0 / shape[0]).to(**f64).reshape(-1, 1, 1)
+    ky = torch.fft.fftfreq(shape[1], d=1.0 / shape[1]).to(**f64).reshape(1, -1, 1)
+    kx = torch.fft.rfftfreq(shape[2], d=1.0 / shape[2]).to(**f64).reshape(1, 1, -1)
+    k2 = kz * kz + ky * ky + kx * kx
+    kmag = torch.sqrt(k2)
+    e = torch.as_tensor(spectrum(kmag.cpu().numpy()), device=device)
+    amp = torch.where(kmag > 0, torch.sqrt(e / torch.where(kmag > 0, 4.0 * math.pi * k2, torch.ones_like(k2))),
+                      torch.zeros_like(kmag))
+    del e
+    uh = [torch.fft.rfftn(torch.randn(shape, generator=g, **f64)) * amp for _ in range(3)]
+    kvec = (kx, ky, kz)
+    safe = torch.where(k2 > 0, k2, torch.ones_like(k2))
+    kdotu = uh[0] * kx + uh[1] * ky + uh[2] * kz
+    keep = (k2 > 0) & (kz.abs() != shape[0] // 2) & (ky.abs() != shape[1] // 2) & (kx.abs() != shape[2] // 2)
+    out = torch.empty((3,) + shape, device=device, dtype=torch.float32)
+    ss = 0.0
+    for i in range(3):
+        v = torch.where(keep, uh[i] - kvec[i] * kdotu / safe, torch.zeros_like(uh[i]))
+        ui = torch.fft.irfftn(v, s=shape)
+        ss += float(torch.sum(ui * ui))
+        out[i] = ui.float()
+        del v, ui
+    return out / math.sqrt(ss / math.prod(shape))

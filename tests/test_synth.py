@@ -54,3 +54,16 @@ def test_uneven_batch_sizes():
     ok = set(fields.smooth_sizes(64, 4096))
     assert all(s[0] in ok and s[0] % 4 == 0 for s in shapes)
     assert shapes == fields.uneven_batch(0) and shapes != fields.uneven_batch(1)
+
+
+def test_velocity_torch_recipe_solenoidal_and_normalised():
+    import torch
+    v = fields.random_velocity_field_torch((24, 16, 32), 2, fields.spectrum_3d_kolmogorov, device="cpu")
+    v = v.double().numpy()
+    assert v.shape == (3, 24, 16, 32)
+    assert abs(np.sqrt(np.mean(np.sum(v * v, axis=0))) - 1.0) < 1e-6
+    kz, ky, kx = np.meshgrid(*[np.fft.fftfreq(n, 1.0 / n) for n in (24, 16, 32)], indexing="ij")
+    div = kx * np.fft.fftn(v[0]) + ky * np.fft.fftn(v[1]) + kz * np.fft.fftn(v[2])
+    assert np.max(np.abs(div)) < 1e-5 * np.max(np.abs(np.fft.fftn(v[0])))
+    w = fields.random_velocity_field_torch((24, 16, 32), 2, fields.spectrum_3d_kolmogorov, device="cpu")
+    assert torch.equal(torch.from_numpy(v).float(), w)
