@@ -62,7 +62,7 @@ def _peaks():
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "passes.cuh", "args.h"):
+    for f in ("fft.cuh", "passes.cuh", "spectral.cuh", "args.h"):
         with open(os.path.join(ROOT, "paper_1707_09177_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -135,6 +135,10 @@ def _pass_bytes(kind, op, P, SP, B, method):
     """Algorithmic bytes one launch must move (each array read or written
     once), float32 fields (4 B) and complex64 spectra (8 B)."""
     v, s = 4 * P * B, 8 * SP * B
+    if kind == "spec":                                 # spectral vectors read + written
+        return {0: 1, 1: 3, 2: 4, 3: 1, 4: 4, 5: 3, 6: 5, 7: 4, 8: 2, 9: 6}[op] * s
+    if kind in ("lfwd", "linv"):
+        return 2 * s
     if kind == "filt":
         return 2 * s                                   # spectrum in, filtered spectrum out
     if kind == "xfwd":
@@ -144,6 +148,20 @@ def _pass_bytes(kind, op, P, SP, B, method):
         rw = {0: (0, 1), 1: (1, 1), 2: (1, 0), 3: (1, 1), 4: (1, 1), 5: (2, 2), 6: (1, 1), 7: (4, 2)}[op]
         return s + (rw[0] + rw[1]) * v
     return 2 * s
+
+
+def _traffic(kind, op, space):
+    """DRAM bytes per launch of a pass kernel from profiles/traffic.json (an ncu
+    capture), or None when absent or taken with other kernel sources."""
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tp):
+        return None
+    with open(tp) as f:
+        td = json.load(f)
+    k = "%s:%s:%d" % (space, kind, op)
+    if td.get("kernel_sha") == _kernel_sha() and k in td.get("bytes_per_launch", {}):
+        return td["bytes_per_launch"][k]
+    return None
 
 
 def _oracle_solve_seconds(ub64, gamma, method, passes):
@@ -203,8 +221,13 @@ def _extra_workloads(gad, dev, extras):
         del u_true
         r, t = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3))
         its = [int(x) for x in r.iterations]
+        rs, ts = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3,
+                                               space="spectral"))
         out["velocity3d_256_f32"] = {"mpoints_s": 3 * n ** 3 / t / 1e6, "ms": t * 1e3, "iterations": its,
-                                     "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches}
+                                     "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches,
+                                     "spectral": {"mpoints_s": 3 * n ** 3 / ts / 1e6, "ms": ts * 1e3,
+                                                  "iterations": [int(x) for x in rs.iterations],
+                                                  "converged": bool(np.all(rs.status == gad.AD_OK))}}
         del ub, r
         torch.cuda.empty_cache()
     if "uneven48" in extras:
@@ -275,8 +298,9 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
     del ut, ubt
     torch.cuda.empty_cache()
 
-    def solve(u0=None):
-        return gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=4000, ndim=3, u0=u0, history=False)
+    def solve(u0=None, space="physical"):
+        return gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=4000, ndim=3, u0=u0, history=False,
+                              space=space)
 
     def timed(fn):
         torch.cuda.synchronize()
@@ -292,6 +316,9 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
     learned, t_solve = timed(lambda: solve(u0))
     u0s = gad.guess_infer(w_stencil, ub, gamma)
     stencil, t_stencil = timed(lambda: solve(u0s))
+    gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=2, ndim=3, history=False, space="spectral")
+    sp_plain, t_sp_plain = timed(lambda: solve(space="spectral"))
+    sp_learned, t_sp_solve = timed(lambda: solve(u0, space="spectral"))
     diff = float(torch.linalg.vector_norm(learned.u - plain.u) / torch.linalg.vector_norm(plain.u))
     pts = 3.0 * n ** 3
     t_learned = t_inf + t_solve
@@ -305,6 +332,13 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
                     "converged": bool(np.all(learned.status == gad.AD_OK))},
         "stencil_start_untrained": {"solve_ms": t_stencil * 1e3,
                                     "iterations": [int(x) for x in stencil.iterations]},
+        "spectral_space": {
+            "plain": {"ms": t_sp_plain * 1e3, "iterations": [int(x) for x in sp_plain.iterations],
+                      "converged": bool(np.all(sp_plain.status == gad.AD_OK))},
+            "learned": {"ms": (t_inf + t_sp_solve) * 1e3, "solve_ms": t_sp_solve * 1e3,
+                        "iterations": [int(x) for x in sp_learned.iterations],
+                        "converged": bool(np.all(sp_learned.status == gad.AD_OK))},
+            "wall_time_ratio_plain_over_learned": t_sp_plain / (t_inf + t_sp_solve)},
         "wall_time_ratio_plain_over_learned": t_plain / t_learned,
         "rel_l2_learned_vs_plain_solution": diff,
         "train": {"pairs": npairs, "shape": [n_train] * 3, "epochs": epochs, "batch": batch, "lr": lr,
@@ -359,6 +393,9 @@ def main():
                     help="drive the iteration loop from the host instead of a graph while node (same kernels; "
                          "profilers cannot see kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--batch", type=int, default=WORKLOAD["batch"], help="fields per GPU")
+    ap.add_argument("--space", default="physical", choices=["physical", "spectral"],
+                    help="iteration space of the timed solve: physical (G by FFT passes every iteration, the "
+                         "paper's formulation) or spectral (iterate on the half spectra, G pointwise)")
     ap.add_argument("--extras", default="methods,3d256,uneven48,learned512",
                     help="comma list of extra measurements on rank 0: methods, 3d256, uneven48, learned512")
     args = ap.parse_args()
@@ -391,8 +428,8 @@ def main():
     out = torch.empty_like(ubar)
     stream = torch.cuda.current_stream()
 
-    def step(method, maxit=3000, tol_=tol):
-        return gad.deconvolve(ubar, gamma, method=method, tol=tol_, maxit=maxit, ndim=2, out=out)
+    def step(method, maxit=3000, tol_=tol, space=args.space):
+        return gad.deconvolve(ubar, gamma, method=method, tol=tol_, maxit=maxit, ndim=2, out=out, space=space)
 
     def barrier():
         if ws > 1:
@@ -429,7 +466,7 @@ def main():
 
     def e2e_step():
         dev_in.copy_(ubar_host, non_blocking=True)
-        r = gad.deconvolve(dev_in, gamma, method=args.method, tol=tol, maxit=3000, ndim=2, out=out)
+        r = gad.deconvolve(dev_in, gamma, method=args.method, tol=tol, maxit=3000, ndim=2, out=out, space=args.space)
         host_out.copy_(out, non_blocking=True)
         torch.cuda.current_stream().synchronize()
         return r
@@ -455,7 +492,8 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "grid": "2048x2048", "batch_per_gpu": B, "gamma": gamma,
-                       "tol": tol, "method": args.method, "dots": "f64 (compensated f32 products)",
+                       "tol": tol, "method": args.method, "space": args.space,
+                       "dots": "f64 (compensated f32 products)",
                        "l2": "inputs %d MiB per vector, > L2 at batch 16; no flush" % (B * P * 4 >> 20),
                        "loop": "host" if args.host_loop else "graph while node",
                        "parallelism": "replicas" if ws > 1 else "1 gpu"},
@@ -466,49 +504,51 @@ def main():
     if rank == 0 and "methods" in extras:
         # comparison methods on the same batch (one timed solve each)
         methods = {}
-        for m, mi in (("cg", 3000), ("bicgstab", 3000), ("vancittert", VC_MAXIT)):
-            step(m, maxit=mi)
+        for m, mi, sp in (("cg", 3000, "physical"), ("bicgstab", 3000, "physical"),
+                          ("vancittert", VC_MAXIT, "physical"), ("cg", 3000, "spectral"),
+                          ("bicgstab", 3000, "spectral"), ("vancittert", VC_MAXIT, "spectral")):
+            step(m, maxit=mi, space=sp)
             torch.cuda.synchronize()
             ev0.record(stream)
-            r = step(m, maxit=mi)
+            r = step(m, maxit=mi, space=sp)
             ev1.record(stream)
             torch.cuda.synchronize()
             t = ev0.elapsed_time(ev1)
             its = [int(x) for x in r.iterations]
             reached = bool(np.all(r.status == gad.AD_OK))
             hfin = [float(r.history[b, its[b]]) for b in range(B)]
-            methods[m] = {"ms": t, "iterations_mean": float(np.mean(its)), "reached_tol": reached,
-                          "mpoints_s": B * P / (t * 1e-3) / 1e6 if reached else None,
-                          "mpoints_s_per_pass": B * P * float(np.mean(its)) / (t * 1e-3) / 1e6,
-                          "h_final_max": max(hfin)}
+            key = m if sp == "physical" else m + "_spectral"
+            methods[key] = {"ms": t, "iterations_mean": float(np.mean(its)), "reached_tol": reached,
+                            "mpoints_s": B * P / (t * 1e-3) / 1e6 if reached else None,
+                            "mpoints_s_per_pass": B * P * float(np.mean(its)) / (t * 1e-3) / 1e6,
+                            "h_final_max": max(hfin), "launches": r.launches}
             if m == "vancittert":
-                methods[m]["maxit"] = VC_MAXIT
+                methods[key]["maxit"] = VC_MAXIT
         line["methods"] = methods
 
     if rank == 0 and not args.no_extras:
         # roofline of the dominant pass kernel, timed live with CUDA events
-        passes = gad.time_passes(n, gamma, B, method=args.method, reps=20)
         kxn = n[1] // 2 + 1
         SP = kxn * n[0]
-        best = max(passes, key=lambda p: p["ms"])
-        total = sum(p["ms"] for p in passes)
         peak, src = _peaks()
-        for p in passes:
-            p["bytes"] = _pass_bytes(p["kind"], p["op"], P, SP, B, args.method)
-            p["gbs"] = p["bytes"] / (p["ms"] * 1e-3) / 1e9
-        traffic = None
-        tp = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tp):
-            with open(tp) as f:
-                td = json.load(f)
-            k = "%s:%d" % (best["kind"], best["op"])
-            if td.get("kernel_sha") == _kernel_sha() and k in td.get("bytes_per_launch", {}):
-                traffic = td["bytes_per_launch"][k]
-        line["roofline"] = {"bound": "hbm", "kernel": "%s(op %d)" % (best["kind"], best["op"]),
-                            "achieved": best["gbs"], "peak": peak, "unit": "GB/s", "frac": best["gbs"] / peak,
-                            "peak_source": src + " hbm_gbs (copy, burst)", "traffic": traffic,
-                            "share_of_iteration": best["ms"] / total,
-                            "passes": [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in passes]}
+
+        def roofline(space):
+            passes = gad.time_passes(n, gamma, B, method=args.method, reps=20, space=space)
+            best = max(passes, key=lambda p: p["ms"])
+            total = sum(p["ms"] for p in passes)
+            for p in passes:
+                p["bytes"] = _pass_bytes(p["kind"], p["op"], P, SP, B, args.method)
+                p["gbs"] = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+            return {"bound": "hbm", "kernel": "%s(op %d)" % (best["kind"], best["op"]),
+                    "achieved": best["gbs"], "peak": peak, "unit": "GB/s", "frac": best["gbs"] / peak,
+                    "peak_source": src + " hbm_gbs (copy, burst)",
+                    "traffic": _traffic(best["kind"], best["op"], space),
+                    "share_of_iteration": best["ms"] / total,
+                    "passes": [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in passes]}
+
+        line["roofline"] = roofline(args.space)
+        other = "spectral" if args.space == "physical" else "physical"
+        line["roofline_" + other] = roofline(other)
 
         # the oracle on this host's cores, bounded sample
         os.environ["OMP_NUM_THREADS"] = "1"

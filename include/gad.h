@@ -57,7 +57,16 @@ typedef enum {
   AD_VANCITTERT = 0,      /* Algorithm 1 */
   AD_CG = 1,              /* Algorithm 3 */
   AD_BICGSTAB = 2,        /* Algorithm 4 */
-  AD_SD = 3               /* Algorithm 2 */
+  AD_SD = 3,              /* Algorithm 2 */
+  /* Flag OR-ed into a method: iterate on the half spectra of the vectors.
+   * G is diagonal in Fourier space (Eq. df2), so each pass is a pointwise
+   * multiply by G_hat with the vector updates and Parseval inner products
+   * fused into one streaming kernel (one for VC, two for SD and CG, three
+   * for BiCGSTAB); u_bar is transformed once before the loop and u once
+   * after it. Same iterates as the physical-space method in exact
+   * arithmetic; in floating point the result differs by rounding. Accepted
+   * by ad_deconvolve, ad_deconvolve_batched, ad_time_pass and ad_autotune. */
+  AD_SPECTRAL = 4
 } ad_method;
 
 typedef enum { AD_F32 = 0, AD_F64 = 1 } ad_dtype;

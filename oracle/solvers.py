@@ -28,6 +28,14 @@ Readings of points the paper leaves open (each applies to every method):
     each update and after each application of G) and float32 scalars where
     they multiply vectors; inner products and scalar recurrences stay in
     float64. precision="f64" is plain float64 throughout.
+  * space="spectral" runs the same steps on the half spectra of the vectors
+    (numpy rfftn layout): G is diagonal in Fourier space (Eq. df2), so it
+    becomes a pointwise multiply by G_hat, and the inner product becomes the
+    Parseval sum (a, b) = (1/P) sum_k w(k_x) Re(a_hat conj(b_hat)) with
+    w = 1 on the k_x = 0 and k_x = N_x/2 planes and 2 elsewhere. u_bar (and
+    u0) are transformed once at the start and u once at the end; the
+    iterates equal those of space="physical" in exact arithmetic. In f32
+    mode the complex vectors are rounded to complex64.
 """
 
 from __future__ import annotations
@@ -37,7 +45,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .spectral import filter_field
+from .spectral import filter_field, transfer_function
 
 STATUS_OK = 0
 STATUS_MAXIT = 1
@@ -69,19 +77,79 @@ class _Arith:
         self.f32 = precision == "f32"
 
     def vec(self, x):
-        x = np.asarray(x, dtype=np.float64)
+        x = np.asarray(x)
+        if np.iscomplexobj(x):
+            x = x.astype(np.complex128)
+            return x.astype(np.complex64).astype(np.complex128) if self.f32 else x
+        x = x.astype(np.float64)
         return x.astype(np.float32).astype(np.float64) if self.f32 else x
 
     def scal(self, a):
         return float(np.float32(a)) if self.f32 else float(a)
 
 
-def _start(ubar, gamma, u0, ar):
+class _Physical:
+    """Vectors are fields on the grid; G by FFT (Eq. df2), plain sums (Eq. inner)."""
+
+    def __init__(self, shape, gamma):
+        self.gamma = gamma
+
+    def G(self, x):
+        return filter_field(x, self.gamma)
+
+    def inner(self, a, b):
+        return inner(a, b)
+
+    def to(self, x):
+        return x
+
+    def back(self, x):
+        return x
+
+
+class _Spectral:
+    """Vectors are half spectra (rfftn over all axes, last axis halved); G is
+    the pointwise multiply by G_hat and (a, b) the weighted Parseval sum."""
+
+    def __init__(self, shape, gamma):
+        self.shape = tuple(shape)
+        nxh = self.shape[-1] // 2 + 1
+        self.gh = transfer_function(self.shape, gamma)[..., :nxh]
+        w = np.full(nxh, 2.0)
+        w[0] = 1.0
+        if self.shape[-1] % 2 == 0:
+            w[-1] = 1.0
+        self.w = w
+        self.p = float(np.prod(self.shape))
+
+    def G(self, x):
+        return self.gh * x
+
+    def inner(self, a, b):
+        return float(np.sum(self.w * np.real(a * np.conj(b)))) / self.p
+
+    def to(self, x):
+        return np.fft.rfftn(np.asarray(x, dtype=np.float64))
+
+    def back(self, x):
+        return np.fft.irfftn(x, s=self.shape, axes=tuple(range(len(self.shape))))
+
+
+def _space(space, shape, gamma):
+    if space == "physical":
+        return _Physical(shape, gamma)
+    if space == "spectral":
+        return _Spectral(shape, gamma)
+    raise ValueError("space must be 'physical' or 'spectral'")
+
+
+def _start(ubar, gamma, u0, ar, sp):
     ubar = ar.vec(ubar)
-    g_ubar = ar.vec(filter_field(ubar, gamma))
-    ref = math.sqrt(inner(ar.vec(ubar - g_ubar), ar.vec(ubar - g_ubar)))
-    u = ubar.copy() if u0 is None else ar.vec(u0)
-    r = ar.vec(ubar - (g_ubar if u0 is None else ar.vec(filter_field(u, gamma))))
+    b = ar.vec(sp.to(ubar))
+    g_b = ar.vec(sp.G(b))
+    ref = math.sqrt(sp.inner(ar.vec(b - g_b), ar.vec(b - g_b)))
+    u = b.copy() if u0 is None else ar.vec(sp.to(ar.vec(u0)))
+    r = ar.vec(b - (g_b if u0 is None else ar.vec(sp.G(u))))
     return ubar, ref, u, r
 
 
@@ -89,7 +157,8 @@ def _h(rr, ref):
     return 0.0 if ref == 0.0 else math.sqrt(max(rr, 0.0)) / ref
 
 
-def _finish(ubar, gamma, u, ref, n, status, hist, trace):
+def _finish(ubar, gamma, u, ref, n, status, hist, trace, sp, ar):
+    u = ar.vec(sp.back(u))
     res = ubar - filter_field(u, gamma)
     tr = math.sqrt(inner(res, res)) / ref if ref > 0 else math.sqrt(inner(res, res))
     return SolveResult(u=u, iterations=n, status=status,
@@ -109,22 +178,23 @@ def _pre_loop(rr0, ref, tol, maxit):
     return None, h0
 
 
-def van_cittert(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+def van_cittert(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, space="physical"):
     """Algorithm 1: u_{n+1} = u_n + r_n, d_n = G r_n, r_{n+1} = r_n - d_n,
     starting from u_0 = u_bar, r_0 = u_bar - G u_0 (Eq. adm2, Eq. res, Eq. ric)."""
     ar = _Arith(precision)
-    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
-    rr = inner(r, r)
+    sp = _space(space, np.shape(ubar), gamma)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar, sp)
+    rr = sp.inner(r, r)
     status, h0 = _pre_loop(rr, ref, tol, maxit)
     hist = [h0]
     trace = {"r": [r.copy()]} if record else {}
     n = 0
     while status is None:
         u = ar.vec(u + r)                        # u_{n+1} = u_n + r_n
-        d = ar.vec(filter_field(r, gamma))       # d_n = G r_n
+        d = ar.vec(sp.G(r))       # d_n = G r_n
         r = ar.vec(r - d)                        # r_{n+1} = r_n - d_n
         n += 1
-        rr = inner(r, r)
+        rr = sp.inner(r, r)
         h = _h(rr, ref)
         hist.append(h)
         if record:
@@ -135,22 +205,23 @@ def van_cittert(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=
             status = STATUS_OK
         elif n >= maxit:
             status = STATUS_MAXIT
-    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace, sp, ar)
 
 
-def steepest_descent(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+def steepest_descent(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, space="physical"):
     """Algorithm 2: d_n = G r_n, alpha_n = (r_n, r_n)/(r_n, d_n) (Eq. sd-a),
     u_{n+1} = u_n + alpha_n r_n (Eq. sd), r_{n+1} = r_n - alpha_n d_n (Eq. rnew1)."""
     ar = _Arith(precision)
-    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
-    rr = inner(r, r)
+    sp = _space(space, np.shape(ubar), gamma)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar, sp)
+    rr = sp.inner(r, r)
     status, h0 = _pre_loop(rr, ref, tol, maxit)
     hist = [h0]
     trace = {"alpha": []} if record else {}
     n = 0
     while status is None:
-        d = ar.vec(filter_field(r, gamma))
-        rd = inner(r, d)
+        d = ar.vec(sp.G(r))
+        rd = sp.inner(r, d)
         alpha = rr / rd if rd != 0.0 else float("nan")
         if not math.isfinite(alpha):
             status = STATUS_BREAKDOWN
@@ -159,7 +230,7 @@ def steepest_descent(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", re
         u = ar.vec(u + a * r)
         r = ar.vec(r - a * d)
         n += 1
-        rr = inner(r, r)
+        rr = sp.inner(r, r)
         h = _h(rr, ref)
         hist.append(h)
         if record:
@@ -170,25 +241,26 @@ def steepest_descent(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", re
             status = STATUS_OK
         elif n >= maxit:
             status = STATUS_MAXIT
-    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace, sp, ar)
 
 
-def conjugate_gradient(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+def conjugate_gradient(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, space="physical"):
     """Algorithm 3: p_0 = r_0, rho_0 = (r_0, r_0); per pass d_n = G p_n,
     alpha_n = rho_n/(p_n, d_n) (Eq. cg-alpha), u_{n+1} = u_n + alpha_n p_n,
     r_{n+1} = r_n - alpha_n d_n (Eq. rnew2), rho_{n+1} = (r_{n+1}, r_{n+1}),
     beta_n = rho_{n+1}/rho_n (Eq. cg-b), p_{n+1} = r_{n+1} + beta_n p_n (Eq. cg4)."""
     ar = _Arith(precision)
-    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
+    sp = _space(space, np.shape(ubar), gamma)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar, sp)
     p = r.copy()
-    rho = inner(r, r)
+    rho = sp.inner(r, r)
     status, h0 = _pre_loop(rho, ref, tol, maxit)
     hist = [h0]
     trace = {"r": [r.copy()], "p": [p.copy()], "d": [], "alpha": [], "beta": [], "u": [u.copy()]} if record else {}
     n = 0
     while status is None:
-        d = ar.vec(filter_field(p, gamma))
-        pd = inner(p, d)
+        d = ar.vec(sp.G(p))
+        pd = sp.inner(p, d)
         alpha = rho / pd if pd != 0.0 else float("nan")
         if not math.isfinite(alpha):
             status = STATUS_BREAKDOWN
@@ -196,7 +268,7 @@ def conjugate_gradient(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", 
         a = ar.scal(alpha)
         u = ar.vec(u + a * p)
         r = ar.vec(r - a * d)
-        rho_new = inner(r, r)
+        rho_new = sp.inner(r, r)
         beta = rho_new / rho
         p = ar.vec(r + ar.scal(beta) * p)
         rho = rho_new
@@ -216,10 +288,10 @@ def conjugate_gradient(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", 
             status = STATUS_OK
         elif n >= maxit:
             status = STATUS_MAXIT
-    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace, sp, ar)
 
 
-def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, space="physical"):
     """Algorithm 4: f_0 = r_0, p_0 = q_0 = 0, alpha_0 = omega_0 = rho_0 = 1; per pass
     rho_{n+1} = (f_0, r_n), beta_n = (alpha_n/omega_n)(rho_{n+1}/rho_n),
     p_{n+1} = r_n + beta_n (p_n - omega_n q_n), q_{n+1} = G p_{n+1},
@@ -228,18 +300,19 @@ def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=Fal
     u_{n+1} = u_n + alpha_{n+1} p_{n+1} + omega_{n+1} s_n,
     r_{n+1} = s_n - omega_{n+1} t_n."""
     ar = _Arith(precision)
-    ubar, ref, u, r = _start(ubar, gamma, u0, ar)
+    sp = _space(space, np.shape(ubar), gamma)
+    ubar, ref, u, r = _start(ubar, gamma, u0, ar, sp)
     f0 = r.copy()
     p = np.zeros_like(r)
     q = np.zeros_like(r)
     alpha = omega = rho = 1.0
-    rr = inner(r, r)
+    rr = sp.inner(r, r)
     status, h0 = _pre_loop(rr, ref, tol, maxit)
     hist = [h0]
     trace = {"s": [], "t": [], "r": [r.copy()], "alpha": [], "omega": [], "rho": []} if record else {}
     n = 0
     while status is None:
-        rho_new = inner(f0, r)
+        rho_new = sp.inner(f0, r)
         if rho_new == 0.0 or not math.isfinite(rho_new):
             status = STATUS_BREAKDOWN
             break
@@ -248,18 +321,18 @@ def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=Fal
             status = STATUS_BREAKDOWN
             break
         p = ar.vec(r + ar.scal(beta) * ar.vec(p - ar.scal(omega) * q))
-        q = ar.vec(filter_field(p, gamma))
-        fq = inner(f0, q)
+        q = ar.vec(sp.G(p))
+        fq = sp.inner(f0, q)
         if fq == 0.0 or not math.isfinite(fq):
             status = STATUS_BREAKDOWN
             break
         alpha = rho_new / fq
         s = ar.vec(r - ar.scal(alpha) * q)
-        ss = inner(s, s)
-        t = ar.vec(filter_field(s, gamma))
-        tt = inner(t, t)
+        ss = sp.inner(s, s)
+        t = ar.vec(sp.G(s))
+        tt = sp.inner(t, t)
         early = _h(ss, ref) <= tol or tt == 0.0
-        omega = 0.0 if early else inner(s, t) / tt
+        omega = 0.0 if early else sp.inner(s, t) / tt
         if not math.isfinite(omega):
             status = STATUS_BREAKDOWN
             break
@@ -267,7 +340,7 @@ def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=Fal
         r = ar.vec(s - ar.scal(omega) * t)
         rho = rho_new
         n += 1
-        rr = inner(r, r)
+        rr = sp.inner(r, r)
         h = _h(rr, ref)
         hist.append(h)
         if record:
@@ -283,7 +356,7 @@ def bicgstab(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=Fal
             status = STATUS_OK
         elif n >= maxit:
             status = STATUS_MAXIT
-    return _finish(ubar, gamma, u, ref, n, status, hist, trace)
+    return _finish(ubar, gamma, u, ref, n, status, hist, trace, sp, ar)
 
 
 _METHODS = {
@@ -294,7 +367,7 @@ _METHODS = {
 }
 
 
-def solve(method, ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False):
+def solve(method, ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, space="physical"):
     """Dispatch by method name: 'vancittert', 'sd', 'cg' or 'bicgstab'."""
     return _METHODS[method](ubar, gamma, tol=tol, maxit=maxit, u0=u0,
-                            precision=precision, record=record)
+                            precision=precision, record=record, space=space)

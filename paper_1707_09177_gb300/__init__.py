@@ -28,13 +28,24 @@ _LIB_PATH = os.path.join(_HERE, "libgad.so")
 AD_OK, AD_MAXIT, AD_BREAKDOWN = 0, 1, 2
 AD_ERR_ARG, AD_ERR_NONFINITE, AD_ERR_CUDA, AD_ERR_TIMEOUT, AD_ERR_NOMEM = -1, -2, -3, -4, -5
 METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3}
+AD_SPECTRAL = 4                     # flag: iterate on the half spectra (G a pointwise multiply)
+SPACES = ("physical", "spectral")
+
+
+def method_code(method, space="physical"):
+    """The C method value for a method name and iteration space."""
+    if method not in METHODS:
+        raise ValueError("method must be one of %s" % sorted(METHODS))
+    if space not in SPACES:
+        raise ValueError("space must be one of %s" % (SPACES,))
+    return METHODS[method] | (AD_SPECTRAL if space == "spectral" else 0)
 AD_F32, AD_F64 = 0, 1
 
 EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvolve_batched", "ad_time_pass",
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
             "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
             "ad_guess_train")
-PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv"}
+PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec"}
 
 
 class ad_grid(ctypes.Structure):
@@ -198,14 +209,14 @@ class Solve:
 
 
 def deconvolve(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, u0=None, ndim=None,
-               out=None, history=True, true_residual=False, stream=None):
-    """Solves G u = u_bar (Section 3, Eq. tau3) for every field of ``ubar``."""
+               out=None, history=True, true_residual=False, stream=None, space="physical"):
+    """Solves G u = u_bar (Section 3, Eq. tau3) for every field of ``ubar``;
+    ``space="spectral"`` iterates on the half spectra (AD_SPECTRAL)."""
     import torch
     lib = load()
     ctx = context(ubar.device.index)
     g, batch, _ = _grid(ubar, ndim, gamma)
-    if method not in METHODS:
-        raise ValueError("method must be one of %s" % sorted(METHODS))
+    code = method_code(method, space)
     if out is None:
         out = torch.empty_like(ubar)
     if u0 is not None and (u0.shape != ubar.shape or u0.dtype != ubar.dtype or not u0.is_contiguous()):
@@ -216,7 +227,7 @@ def deconvolve(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, u0=None, nd
     tr = np.zeros(batch) if true_residual else None
     ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p()
     st = lib.ad_deconvolve(ctx, ctypes.byref(g), ctypes.c_void_p(ubar.data_ptr()), ctypes.c_void_p(out.data_ptr()),
-                           batch, METHODS[method], float(tol), int(maxit),
+                           batch, code, float(tol), int(maxit),
                            ctypes.c_void_p(u0.data_ptr()) if u0 is not None else ctypes.c_void_p(),
                            ptr(its), ptr(sts), ptr(hist), ptr(tr), _stream_ptr(stream))
     _check(st, ctx, per_field=True)
@@ -224,7 +235,8 @@ def deconvolve(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, u0=None, nd
                  launches=int(lib.ad_last_launch_count(ctx)))
 
 
-def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, stream=None, device=None):
+def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, stream=None, device=None,
+                space="physical"):
     """Per-launch time (ms) of every pass kernel of one iteration of ``method``,
     measured by the library with CUDA events in the solve's launch shapes.
     Returns a list of dicts (index, kind, op, ms)."""
@@ -238,13 +250,14 @@ def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, st
     g.dtype = AD_F32 if dtype == "f32" else AD_F64
     g.gamma = float(gamma)
     cnt = ctypes.c_int(0)
-    st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), METHODS[method], -1, 1, _stream_ptr(stream),
+    code = method_code(method, space)
+    st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), code, -1, 1, _stream_ptr(stream),
                           None, None, None, ctypes.byref(cnt))
     _check(st, ctx)
     out = []
     for i in range(cnt.value):
         ms, kind, op = ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
-        st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), METHODS[method], i, int(reps), _stream_ptr(stream),
+        st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), code, i, int(reps), _stream_ptr(stream),
                               ctypes.byref(ms), ctypes.byref(kind), ctypes.byref(op), None)
         _check(st, ctx)
         out.append(dict(index=i, kind=PASS_KINDS[kind.value], op=int(op.value), ms=float(ms.value)))
@@ -252,7 +265,7 @@ def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, st
 
 
 def deconvolve_batched(fields, gammas, method="bicgstab", tol=1e-6, maxit=1000, ndims=None, outs=None,
-                       history=True, stream=None):
+                       history=True, stream=None, space="physical"):
     """Solves G u = u_bar for a list of fields of uneven size in one library
     call (one CUDA graph). ``fields`` is a list of contiguous CUDA tensors,
     each one field ((Ny, Nx) or (Nz, Ny, Nx)); ``gammas`` a list of filter
@@ -277,14 +290,15 @@ def deconvolve_batched(fields, gammas, method="bicgstab", tol=1e-6, maxit=1000, 
     sts = np.zeros(n, dtype=np.int32)
     hist = [np.full(int(maxit) + 1, np.nan) for _ in range(n)] if history else None
     phist = (ctypes.c_void_p * n)(*[h.ctypes.data for h in hist]) if history else None
-    st = lib.ad_deconvolve_batched(ctx, n, grids, pin, pout, METHODS[method], float(tol), int(maxit),
+    st = lib.ad_deconvolve_batched(ctx, n, grids, pin, pout, method_code(method, space), float(tol), int(maxit),
                                    ctypes.c_void_p(its.ctypes.data), ctypes.c_void_p(sts.ctypes.data),
                                    phist, _stream_ptr(stream))
     _check(st, ctx, per_field=True)
     return outs, its, sts, hist
 
 
-def autotune(shape=None, gamma=0.1, batch=1, method="bicgstab", dtype="f32", for_batched=False, device=None):
+def autotune(shape=None, gamma=0.1, batch=1, method="bicgstab", dtype="f32", for_batched=False, device=None,
+             space="physical"):
     """Tunes the tile widths of the plan for (shape, batch) by timing every
     admissible width per pass (``shape=None``: only set whether batched solves
     tune their plans)."""
@@ -299,7 +313,7 @@ def autotune(shape=None, gamma=0.1, batch=1, method="bicgstab", dtype="f32", for
             g.n[i] = int(rev[i])
         g.dtype = AD_F32 if dtype == "f32" else AD_F64
         g.gamma = float(gamma)
-    st = lib.ad_autotune(ctx, ctypes.byref(g) if g is not None else None, int(batch), METHODS[method],
+    st = lib.ad_autotune(ctx, ctypes.byref(g) if g is not None else None, int(batch), method_code(method, space),
                          1 if for_batched else 0)
     _check(st, ctx)
 

@@ -64,6 +64,8 @@ struct Plan {
   const void* twx = nullptr;
   void *S1 = nullptr, *S2 = nullptr;
   void *R = nullptr, *Pv = nullptr, *Q = nullptr, *Sv = nullptr, *F0 = nullptr;
+  void *Bh = nullptr, *Uh = nullptr, *Rh = nullptr, *Ph = nullptr, *F0h = nullptr;  // spectral-space vectors
+  PassCfg sp;                        // spectral-space pass launch shape
   void* Uscratch = nullptr;          // stands in for u when a single pass is timed
   void *Bin = nullptr, *Bout = nullptr;   // batched solves: the group's fields gathered contiguously
   FieldState* st = nullptr;
@@ -72,7 +74,8 @@ struct Plan {
   double* hist = nullptr;
   int hist_cap = 0;
   unsigned maxblk = 0;               // capacity of part (blocks per field)
-  bool tuned = false;
+  bool tuned = false;                // tile widths of the FFT passes tuned
+  bool sp_tuned = false;             // spectral-pass launch width tuned
   std::vector<void*> owned;
 };
 
@@ -276,6 +279,11 @@ bool choose_tile(int L, int E, int slots, int div, size_t csize, PassCfg& pc) {
 
 int pick_E(int L) { return (L % 3 == 0) ? 24 : 16; }
 
+// A method value: one of AD_VANCITTERT .. AD_SD, optionally OR-ed with AD_SPECTRAL.
+bool method_ok(int m) { return m >= 0 && (m & ~(AD_SPECTRAL | 3)) == 0; }
+int method_base(int m) { return m & 3; }
+bool method_spectral(int m) { return (m & AD_SPECTRAL) != 0; }
+
 std::string plan_key(const ad_grid* g, int batch) {
   char buf[256];
   snprintf(buf, sizeof buf, "%d:%lld:%lld:%lld:%d:%a:%d", g->ndim, (long long)g->n[0], (long long)g->n[1],
@@ -388,6 +396,30 @@ ad_status ensure_vectors(ad_ctx* ctx, Plan* p) {
       (s = dmalloc(ctx, p, &p->Q, vb)) != AD_OK || (s = dmalloc(ctx, p, &p->Sv, vb)) != AD_OK ||
       (s = dmalloc(ctx, p, &p->F0, vb)) != AD_OK)
     return s;
+  return AD_OK;
+}
+
+// Spectral-space vectors (complex half spectra, SP per field) and the launch
+// shape of the streaming spectral passes: each block streams a contiguous
+// range of sequences, about 2048 element pairs at least, at most 1216 blocks
+// (8 per SM) per field and never more than the partial-dot capacity. The
+// shape depends on the grid only, so a field's result does not depend on
+// the batch it is solved in.
+ad_status ensure_spectral(ad_ctx* ctx, Plan* p) {
+  if (p->Bh) return AD_OK;
+  const size_t sb = (size_t)p->SP * p->batch * (p->f64 ? 16 : 8);
+  ad_status s;
+  if ((s = dmalloc(ctx, p, &p->Bh, sb)) != AD_OK || (s = dmalloc(ctx, p, &p->Uh, sb)) != AD_OK ||
+      (s = dmalloc(ctx, p, &p->Rh, sb)) != AD_OK || (s = dmalloc(ctx, p, &p->Ph, sb)) != AD_OK ||
+      (s = dmalloc(ctx, p, &p->F0h, sb)) != AD_OK)
+    return s;
+  const long long pairs = p->SP / 2;
+  long long nb = (pairs + 2047) / 2048;
+  nb = std::min<long long>(nb, 1216);
+  nb = std::min<long long>(nb, (long long)p->maxblk);
+  p->sp = PassCfg{};
+  p->sp.T = 256;
+  p->sp.grid = dim3((unsigned)std::max<long long>(nb, 1), p->batch);
   return AD_OK;
 }
 
@@ -512,12 +544,135 @@ struct SolveIO {
   const void* ubar;
   void* u;
   const void* u0;
-  int method;
+  int method;           // AD_VANCITTERT .. AD_SD (the AD_SPECTRAL flag goes to `spectral`)
   bool want_true;
+  bool spectral = false;
+};
+
+// ---------------------------------------------------------------------------
+// Spectral-space solve: transforms, streaming passes, init/body/finish.
+
+// x = u_bar or u0 -> its half spectrum `out` (x pass, 3D y pass, last-axis pass).
+template <typename T>
+ad_status enqueue_fwd_transform(ad_ctx* ctx, Plan* p, cudaStream_t s, const void* x, void* out, int* nl) {
+  Common c0;                            // no solver state: every field runs
+  PassArgs<T> a = base_args<T>(p, c0);
+  set_pass(a, p->xf);
+  a.op = XF_COPY; a.A = (const T*)x;
+  CK(issue<T>(ctx, PK_XFWD, p->xf, s, a));
+  ++*nl;
+  if (p->ndim == 3) {
+    set_pass(a, p->yf);
+    CK(issue<T>(ctx, PK_YFWD, p->yf, s, a));
+    ++*nl;
+  }
+  set_pass(a, p->fl);
+  a.O1 = (T*)out;
+  CK(issue<T>(ctx, PK_LFWD, p->fl, s, a));
+  ++*nl;
+  return AD_OK;
+}
+
+// half spectrum `hat` -> physical field x (scaled by 1/P on the way).
+template <typename T>
+ad_status enqueue_inv_transform(ad_ctx* ctx, Plan* p, cudaStream_t s, const void* hat, void* x, int* nl) {
+  Common c0;
+  PassArgs<T> a = base_args<T>(p, c0);
+  set_pass(a, p->fl);
+  a.A = (const T*)hat;
+  CK(issue<T>(ctx, PK_LINV, p->fl, s, a));
+  ++*nl;
+  a.A = nullptr;
+  if (p->ndim == 3) {
+    set_pass(a, p->yi);
+    CK(issue<T>(ctx, PK_YINV, p->yi, s, a));
+    ++*nl;
+  }
+  set_pass(a, p->xi);
+  a.op = XI_STORE; a.O1 = (T*)x;
+  CK(issue<T>(ctx, PK_XINV, p->xi, s, a));
+  ++*nl;
+  return AD_OK;
+}
+
+struct Spec {
+  int op = SP_REF, stage = SS_NONE, ndots = 1;
+  const void* A = nullptr; const void* B = nullptr;
+  void* O1 = nullptr; void* O2 = nullptr; void* O3 = nullptr;
+  bool clear_cond = false, set_cond = false;
 };
 
 template <typename T>
+ad_status enqueue_spec(ad_ctx* ctx, Plan* p, cudaStream_t s, const Spec& sp, const Common& c, int* nl) {
+  PassArgs<T> a = base_args<T>(p, c);
+  a.op = sp.op; a.stage = sp.stage; a.ndots = sp.ndots;
+  a.A = (const T*)sp.A; a.B = (const T*)sp.B;
+  a.O1 = (T*)sp.O1; a.O2 = (T*)sp.O2; a.O3 = (T*)sp.O3;
+  a.inv_p = 1.0 / (double)p->P;        // Parseval
+  a.clear_cond = (sp.clear_cond && c.in_graph) ? 1 : 0;
+  a.set_cond = (sp.set_cond && c.in_graph) ? 1 : 0;
+  CK(issue<T>(ctx, PK_SPEC, p->sp, s, a));
+  ++*nl;
+  return AD_OK;
+}
+
+template <typename T>
+ad_status enqueue_spec_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  CK(launch_reset_state(p->st, p->batch, s));
+  ++*nl;
+  ad_status r;
+  if ((r = enqueue_fwd_transform<T>(ctx, p, s, io.ubar, p->Bh, nl)) != AD_OK) return r;
+  if (io.u0) {
+    if ((r = enqueue_fwd_transform<T>(ctx, p, s, io.u0, p->Uh, nl)) != AD_OK) return r;
+    Spec ref; ref.op = SP_REF; ref.stage = SS_REF; ref.A = p->Bh;
+    if ((r = enqueue_spec<T>(ctx, p, s, ref, c, nl)) != AD_OK) return r;
+  }
+  Spec in; in.op = SP_INIT; in.stage = SS_INIT; in.A = p->Bh;
+  in.B = io.u0 ? p->Uh : nullptr;
+  in.O1 = io.u0 ? nullptr : p->Uh;
+  in.O2 = p->Rh;
+  in.O3 = io.method == AD_BICGSTAB ? p->F0h : nullptr;
+  return enqueue_spec<T>(ctx, p, s, in, c, nl);
+}
+
+template <typename T>
+ad_status enqueue_spec_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  ad_status r;
+  switch (io.method) {
+    case AD_VANCITTERT: {
+      Spec k; k.op = SP_VC; k.stage = SS_VC; k.O1 = p->Uh; k.O2 = p->Rh; k.clear_cond = k.set_cond = true;
+      return enqueue_spec<T>(ctx, p, s, k, c, nl);
+    }
+    case AD_SD: {
+      Spec k1; k1.op = SP_SD_A; k1.stage = SS_SD_ALPHA; k1.A = p->Rh; k1.clear_cond = true;
+      if ((r = enqueue_spec<T>(ctx, p, s, k1, c, nl)) != AD_OK) return r;
+      Spec k2; k2.op = SP_SD; k2.stage = SS_VC; k2.O1 = p->Uh; k2.O2 = p->Rh; k2.set_cond = true;
+      return enqueue_spec<T>(ctx, p, s, k2, c, nl);
+    }
+    case AD_CG: {
+      Spec k1; k1.op = SP_CG_P; k1.stage = SS_CG_ALPHA; k1.A = p->Rh; k1.O1 = p->Ph; k1.clear_cond = true;
+      if ((r = enqueue_spec<T>(ctx, p, s, k1, c, nl)) != AD_OK) return r;
+      Spec k2; k2.op = SP_CG; k2.stage = SS_CG_BETA; k2.A = p->Ph; k2.O1 = p->Uh; k2.O2 = p->Rh; k2.set_cond = true;
+      return enqueue_spec<T>(ctx, p, s, k2, c, nl);
+    }
+    case AD_BICGSTAB: {
+      Spec k1; k1.op = SP_BI_P; k1.stage = SS_BI_ALPHA; k1.A = p->Rh; k1.B = p->F0h; k1.O1 = p->Ph;
+      k1.clear_cond = true;
+      if ((r = enqueue_spec<T>(ctx, p, s, k1, c, nl)) != AD_OK) return r;
+      Spec k2; k2.op = SP_BI_S; k2.stage = SS_BI_OMEGA; k2.ndots = 3; k2.A = p->Rh; k2.B = p->Ph;
+      if ((r = enqueue_spec<T>(ctx, p, s, k2, c, nl)) != AD_OK) return r;
+      Spec k3; k3.op = SP_BI_END; k3.stage = SS_BI_END; k3.ndots = 2; k3.A = p->Ph; k3.B = p->F0h;
+      k3.O1 = p->Uh; k3.O2 = p->Rh; k3.set_cond = true;
+      return enqueue_spec<T>(ctx, p, s, k3, c, nl);
+    }
+    default:
+      return fail(ctx, AD_ERR_ARG, "unknown method");
+  }
+}
+
+template <typename T>
 ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  if (io.spectral) return enqueue_spec_init<T>(ctx, p, s, io, c, nl);
   CK(launch_reset_state(p->st, p->batch, s));
   ++*nl;
   ad_status r;
@@ -534,6 +689,7 @@ ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, 
 
 template <typename T>
 ad_status enqueue_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  if (io.spectral) return enqueue_spec_body<T>(ctx, p, s, io, c, nl);
   ad_status r;
   switch (io.method) {
     case AD_VANCITTERT: {          // Algorithm 1: u += r; d = G r; r -= d
@@ -570,7 +726,10 @@ ad_status enqueue_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, 
 
 template <typename T>
 ad_status enqueue_finish(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
-  if (io.method == AD_CG) {
+  if (io.spectral) {
+    ad_status r = enqueue_inv_transform<T>(ctx, p, s, p->Uh, io.u, nl);
+    if (r != AD_OK) return r;
+  } else if (io.method == AD_CG) {
     CK(launch_cg_finish<T>((T*)io.u, (const T*)p->Pv, p->st, p->P, p->batch, s));
     ++*nl;
   }
@@ -660,8 +819,8 @@ ad_status run_solve(ad_ctx* ctx, Plan* p, const SolveIO& io, double tol, int max
   ad_status st;
   if (ctx->use_graph) {
     char buf[256];
-    snprintf(buf, sizeof buf, "|%d|%a|%d|%p|%p|%p|%d", io.method, tol, maxit, io.ubar, io.u, io.u0,
-             io.want_true ? 1 : 0);
+    snprintf(buf, sizeof buf, "|%d|%d|%a|%d|%p|%p|%p|%d", io.method, io.spectral ? 1 : 0, tol, maxit, io.ubar,
+             io.u, io.u0, io.want_true ? 1 : 0);
     char pk[128];
     snprintf(pk, sizeof pk, "%p", (void*)p);
     const std::string gkey = std::string(pk) + buf;
@@ -738,7 +897,7 @@ double time_kind(ad_ctx* ctx, Plan* p, int method, int kind, int reps) {
   Common c;
   c.st = p->st;
   c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method; c.cfg.hist = p->hist; c.cfg.hist_ld = p->hist_cap;
-  SolveIO io{p->F0, p->Uscratch, nullptr, method, false};
+  SolveIO io{p->F0, p->Uscratch, nullptr, method_base(method), false, method_spectral(method)};
   int nl = 0;
   const ad_status s = enqueue_body<T>(ctx, p, nullptr, io, c, &nl);
   ctx->record = nullptr;
@@ -775,6 +934,31 @@ ad_status autotune_plan(ad_ctx* ctx, Plan* p, int method, int reps) {
   if ((s = ensure_vectors(ctx, p)) != AD_OK || (s = ensure_hist(ctx, p, 1)) != AD_OK) return s;
   if (!p->Uscratch && (s = dmalloc(ctx, p, &p->Uscratch, (size_t)p->P * p->batch * (p->f64 ? 8 : 4))) != AD_OK)
     return s;
+  if (method_spectral(method)) {
+    // spectral space: the passes stream; tune the blocks per field (element
+    // pairs per block 512 .. 32768), timing the iteration's spectral passes
+    if ((s = ensure_spectral(ctx, p)) != AD_OK) return s;
+    const long long pairs = p->SP / 2;
+    PassCfg best = p->sp;
+    double best_ms = -1.0;
+    for (long long per = 512; per <= 32768; per *= 2) {
+      long long nb = std::min<long long>((pairs + per - 1) / per, std::min<long long>(4864, p->maxblk));
+      nb = std::max<long long>(nb, 1);
+      PassCfg trial = p->sp;
+      trial.grid.x = (unsigned)nb;
+      const PassCfg keep = p->sp;
+      p->sp = trial;
+      const double ms = p->f64 ? time_kind<double>(ctx, p, method, PK_SPEC, reps)
+                               : time_kind<float>(ctx, p, method, PK_SPEC, reps);
+      p->sp = keep;
+      if (ms > 0.0 && (best_ms < 0.0 || ms < best_ms)) { best_ms = ms; best = trial; }
+    }
+    p->sp = best;
+    CK(cudaDeviceSynchronize());
+    drop_graphs(ctx);
+    p->sp_tuned = true;
+    return AD_OK;
+  }
   const int M = p->nx / 2;
   const int Lf = p->ndim == 3 ? p->nz : p->ny;
   std::vector<TileSlot> slots = {{&p->xf, PK_XFWD, M, M + 1, pow2_part(p->ny)},
@@ -932,7 +1116,7 @@ ad_status capture_group(ad_ctx* ctx, BatchedGroup& gr, cudaStream_t s, cudaGraph
   c.st = p->st;
   c.cfg.tol = tol;
   c.cfg.maxit = maxit;
-  c.cfg.method = method;
+  c.cfg.method = method_base(method);
   c.cfg.hist = p->hist;
   c.cfg.hist_ld = p->hist_cap;
   c.cond = h;
@@ -940,7 +1124,7 @@ ad_status capture_group(ad_ctx* ctx, BatchedGroup& gr, cudaStream_t s, cudaGraph
   const size_t bytes = (size_t)p->P * sizeof(T);
   for (size_t k = 0; k < gr.fields.size(); ++k)
     CK(cudaMemcpyAsync((char*)p->Bin + k * bytes, ubar[gr.fields[k]], bytes, cudaMemcpyDeviceToDevice, s));
-  SolveIO io{p->Bin, p->Bout, nullptr, method, false};
+  SolveIO io{p->Bin, p->Bout, nullptr, method_base(method), false, method_spectral(method)};
   ad_status st = enqueue_init<T>(ctx, p, s, io, c, &gr.n_init);
   if (st != AD_OK) return st;
   cudaStreamCaptureStatus cs;
@@ -1057,20 +1241,22 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
   if (!ctx) return AD_ERR_ARG;
   ad_status s = check_grid(ctx, grid);
   if (s != AD_OK) return s;
-  if (batch < 1 || reps < 1 || method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "bad batch, reps or method");
+  if (batch < 1 || reps < 1 || !method_ok(method)) return fail(ctx, AD_ERR_ARG, "bad batch, reps or method");
   CK(cudaSetDevice(ctx->device));
   Plan* p = nullptr;
   if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
   if ((s = ensure_vectors(ctx, p)) != AD_OK) return s;
   if ((s = ensure_hist(ctx, p, 1)) != AD_OK) return s;
   if (!p->Uscratch && (s = dmalloc(ctx, p, &p->Uscratch, (size_t)p->P * p->batch * (p->f64 ? 8 : 4))) != AD_OK) return s;
+  if (method_spectral(method) && (s = ensure_spectral(ctx, p)) != AD_OK) return s;
   // record one iteration body on internal buffers only
   std::vector<LaunchRec> rec;
   ctx->record = &rec;
   Common c;
   c.st = p->st;
-  c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method; c.cfg.hist = p->hist; c.cfg.hist_ld = p->hist_cap;
-  SolveIO io{p->F0, p->Uscratch, nullptr, (int)method, false};
+  c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method_base(method); c.cfg.hist = p->hist;
+  c.cfg.hist_ld = p->hist_cap;
+  SolveIO io{p->F0, p->Uscratch, nullptr, method_base(method), false, method_spectral(method)};
   int nl = 0;
   s = p->f64 ? enqueue_body<double>(ctx, p, nullptr, io, c, &nl) : enqueue_body<float>(ctx, p, nullptr, io, c, &nl);
   ctx->record = nullptr;
@@ -1113,7 +1299,7 @@ ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, 
   if (nfields < 0) return fail(ctx, AD_ERR_ARG, "nfields < 0");
   if (nfields == 0) { ctx->launches = 0; return AD_OK; }
   if (!grids || !ubar || !u_out) return fail(ctx, AD_ERR_ARG, "NULL array argument");
-  if (method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "unknown method");
+  if (!method_ok(method)) return fail(ctx, AD_ERR_ARG, "unknown method");
   if (maxit < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return fail(ctx, AD_ERR_ARG, "need maxit >= 0 and finite tol >= 0");
   ad_status s;
   for (int i = 0; i < nfields; ++i) {
@@ -1142,7 +1328,9 @@ ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, 
     Plan* p = nullptr;
     if ((s = get_plan(ctx, &grids[members[j][0]], (int)members[j].size(), &p)) != AD_OK) return s;
     if ((s = ensure_vectors(ctx, p)) != AD_OK || (s = ensure_io(ctx, p)) != AD_OK) return s;
-    if (ctx->autotune && !p->tuned && (s = autotune_plan(ctx, p, (int)method, 10)) != AD_OK) return s;
+    if (method_spectral(method) && (s = ensure_spectral(ctx, p)) != AD_OK) return s;
+    const bool tuned = method_spectral(method) ? p->sp_tuned : p->tuned;
+    if (ctx->autotune && !tuned && (s = autotune_plan(ctx, p, (int)method, 10)) != AD_OK) return s;
     groups[j].p = p;
     groups[j].fields = members[j];
   }
@@ -1203,7 +1391,7 @@ ad_status ad_autotune(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method met
   if (!grid) return AD_OK;
   ad_status s = check_grid(ctx, grid);
   if (s != AD_OK) return s;
-  if (batch < 1 || method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "bad batch or method");
+  if (batch < 1 || !method_ok(method)) return fail(ctx, AD_ERR_ARG, "bad batch or method");
   CK(cudaSetDevice(ctx->device));
   Plan* p = nullptr;
   if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
@@ -1402,7 +1590,7 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
   ad_status s = check_grid(ctx, grid);
   if (s != AD_OK) return s;
   if (batch < 0) return fail(ctx, AD_ERR_ARG, "batch < 0");
-  if (method < AD_VANCITTERT || method > AD_SD) return fail(ctx, AD_ERR_ARG, "unknown method");
+  if (!method_ok(method)) return fail(ctx, AD_ERR_ARG, "unknown method");
   if (maxit < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return fail(ctx, AD_ERR_ARG, "need maxit >= 0 and finite tol >= 0");
   if (batch == 0) { ctx->launches = 0; return AD_OK; }
   if (!ubar || !u_out) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
@@ -1414,8 +1602,9 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
   if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK) return s;
   if ((s = ensure_vectors(ctx, p)) != AD_OK) return s;
   if ((s = ensure_hist(ctx, p, maxit)) != AD_OK) return s;
+  if (method_spectral(method) && (s = ensure_spectral(ctx, p)) != AD_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  SolveIO io{ubar, u_out, u0, (int)method, true_res != nullptr};
+  SolveIO io{ubar, u_out, u0, method_base(method), true_res != nullptr, method_spectral(method)};
   int loops = 0, n_body = 0;
   s = p->f64 ? run_solve<double>(ctx, p, io, tol, maxit, st, &loops, &n_body)
              : run_solve<float>(ctx, p, io, tol, maxit, st, &loops, &n_body);

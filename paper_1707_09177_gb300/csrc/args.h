@@ -53,6 +53,23 @@ enum FiOp : int {
   FI_SST = 2,    // (s, s), (s, G s), (G s, G s)
 };
 
+// Spectral-space pass opcodes (the Krylov iteration on the half spectrum,
+// G a pointwise multiply by G_hat(k)). Vectors are complex spectra in the
+// layout of the last-axis transform: 2D [kx][ky], 3D [kx][ky][kz].
+enum SpOp : int {
+  SP_REF = 0,     // d = (b - G b, b - G b)                                  A = b
+  SP_INIT = 1,    // r = b - G x, x = B (u0) or A (b); O1 = b (no u0), O2 = r, O3 = r (BiCGSTAB f0); d = (r, r)
+  SP_VC = 2,      // Algorithm 1: O1 += O2; O2 -= G O2; d = (O2, O2)
+  SP_SD_A = 3,    // Algorithm 2: d = (A, G A)
+  SP_SD = 4,      // Algorithm 2: O1 += alpha O2; O2 -= alpha G O2; d = (O2, O2)
+  SP_CG_P = 5,    // Algorithm 3: O1 = A (first pass) or A + beta O1; d = (O1, G O1)
+  SP_CG = 6,      // Algorithm 3: O1 += alpha A; O2 -= alpha G A; d = (O2, O2)
+  SP_BI_P = 7,    // Algorithm 4: O1 = A (first) or A + beta (O1 - omega G O1); d = (B, G O1)
+  SP_BI_S = 8,    // Algorithm 4: s = A - alpha G B, t = G s; d = (s, s), (s, t), (t, t)
+  SP_BI_END = 9,  // Algorithm 4: s, t from O2 and A; O1 += alpha A + omega s; O2 = s - omega t;
+                  //              d = (O2, O2), (B, O2)
+};
+
 template <typename T>
 struct PassArgs {
   int nx, ny, nz, kxn;       // real grid and kxn = nx/2 + 1

@@ -4,6 +4,7 @@
 
 #include "launch.h"
 #include "passes.cuh"
+#include "spectral.cuh"
 
 namespace gad {
 
@@ -17,6 +18,8 @@ static cudaError_t launch_pass_e(int kind, dim3 grid, int threads, size_t smem, 
     case PK_FILT: fn = k_filt<T, E>; break;
     case PK_YFWD: fn = k_yfwd<T, E>; break;
     case PK_YINV: fn = k_yinv<T, E>; break;
+    case PK_LFWD: fn = k_lfwd<T, E>; break;
+    case PK_LINV: fn = k_linv<T, E>; break;
     default: return cudaErrorInvalidValue;
   }
   if (smem > 48 * 1024) {
@@ -30,6 +33,7 @@ static cudaError_t launch_pass_e(int kind, dim3 grid, int threads, size_t smem, 
 template <typename T>
 cudaError_t launch_pass(int kind, int E, dim3 grid, int threads, size_t smem, cudaStream_t s,
                         const PassArgs<T>& a) {
+  if (kind == PK_SPEC) return launch_spec<T>(grid, s, a);
   if (E == 16) return launch_pass_e<T, 16>(kind, grid, threads, smem, s, a);
   if (E == 24) return launch_pass_e<T, 24>(kind, grid, threads, smem, s, a);
   return cudaErrorInvalidValue;

@@ -8,7 +8,12 @@
 
 namespace gad {
 
-enum PassKind : int { PK_XFWD = 0, PK_XINV = 1, PK_FILT = 2, PK_YFWD = 3, PK_YINV = 4 };
+enum PassKind : int {
+  PK_XFWD = 0, PK_XINV = 1, PK_FILT = 2, PK_YFWD = 3, PK_YINV = 4,
+  PK_LFWD = 5,   // forward FFT along the last axis, S1 (2D) / S2 (3D) -> spectral vector O1
+  PK_LINV = 6,   // inverse FFT along the last axis, spectral vector A (scaled by 1/P) -> S1 / S2
+  PK_SPEC = 7,   // spectral-space Krylov pass (SpOp), 256 threads, no shared memory
+};
 
 // Launches pass `kind` with per-thread element count E (16 or 24). Returns the
 // launch error (cudaSuccess when enqueued).

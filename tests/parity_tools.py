@@ -97,3 +97,58 @@ def count_ok(n_gpu, base, runs):
         return n_gpu == lo, counts
     r = hi - lo
     return lo - r - 1 <= n_gpu <= hi + r + 1, counts
+
+
+# --- the spectral-space variant ------------------------------------------------
+# The oracle's space="spectral" mode stores the half spectra (complex64 in
+# float32 mode) but transforms in float64; the GPU transforms in the field's
+# precision. These helpers make the transforms precision-matched and build the
+# ensemble from periodic shifts of the input itself: a shift is a phase
+# rotation of every mode, which changes how each stored coefficient rounds
+# (whereas the storage rounding of a real field commutes with shifts).
+
+@contextlib.contextmanager
+def spectral_transforms(precision):
+    """Within the block the oracle's spectral space transforms u_bar, u0 and
+    u with single-precision FFTs when `precision` is f32."""
+    if precision != "f32":
+        yield
+        return
+    cls = _osv._Spectral
+    to0, back0 = cls.to, cls.back
+
+    def to(self, x):
+        return scipy.fft.rfftn(np.asarray(x, dtype=np.float32)).astype(np.complex128)
+
+    def back(self, x):
+        y = scipy.fft.irfftn(np.asarray(x).astype(np.complex64), s=self.shape, axes=tuple(range(len(self.shape))))
+        return y.astype(np.float64)
+
+    cls.to, cls.back = to, back
+    try:
+        yield
+    finally:
+        cls.to, cls.back = to0, back0
+
+
+# Wider shifts than SHIFTS: a phase rotation by a large shift re-rounds every
+# stored coefficient, and at gamma = 0.01 a few samples underestimate how far
+# equally valid float32 runs of BiCGSTAB drift apart.
+SHIFTS_SPECTRAL = [(0, 0, 0), (1, 3, 2), (5, 2, 7), (11, 7, 3), (37, 101, 13), (64, 17, 29), (90, 211, 5),
+                   (123, 45, 61), (200, 133, 77)]
+
+
+def ensemble_runs_spectral(method, ub, gamma, tol, maxit, precision, u0=None, shifts=SHIFTS_SPECTRAL):
+    """The precision-matched spectral-space oracle on u_bar and on shifted
+    copies of it (results shifted back)."""
+    out = []
+    ax = tuple(range(ub.ndim))
+    with spectral_transforms(precision):
+        for sh in shifts:
+            s = tuple(sh[: ub.ndim])
+            back = tuple(-x for x in s)
+            r = oracle.solve(method, np.roll(ub, s, ax), gamma, tol=tol, maxit=maxit,
+                             u0=None if u0 is None else np.roll(u0, s, ax), precision=precision, space="spectral")
+            r.u = np.roll(r.u, back, ax)
+            out.append(r)
+    return out[0], out[1:]

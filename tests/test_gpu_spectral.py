@@ -1,0 +1,291 @@
+"""GPU parity of the spectral-space variant (AD_SPECTRAL: Algorithms 1-4
+iterated on the half spectra, G a pointwise multiply by G_hat) against the
+CPU oracle's spectral-space mode (pinned to its physical-space algorithms in
+tests/test_oracle_solvers.py):
+  * one pass: relative L2 <= 1e-5 (float32) or <= 1e-12 (float64) against
+    the float64 oracle;
+  * more passes and tolerance-stopped solves: within max(1e-5 or 1e-12,
+    10 x the spread of the precision-matched spectral oracle over periodic
+    shifts of the input -- see tests/parity_tools.py);
+  * iteration counts: exact when that oracle's count is the same for every
+    shift, else within its spread widened by the spread (+1).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import fields
+from parity_tools import count_ok, field_tolerance, history_tolerance
+from parity_tools import ensemble_runs_spectral as ensemble_runs
+
+pytestmark = pytest.mark.gpu
+
+METHODS = ["vancittert", "sd", "cg", "bicgstab"]
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _problem(shape, seed, gamma, dtype=np.float32):
+    if len(shape) == 3:
+        u = fields.random_velocity_field(shape, seed, fields.spectrum_3d_kolmogorov)[0]
+    else:
+        u = fields.random_scalar_field(shape, seed, fields.spectrum_2d_kraichnan)
+    ub = oracle.filter_field(u, gamma).astype(dtype)
+    return u, ub
+
+
+def _to_gpu(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _solve(gad, ub, gamma, **kw):
+    kw.setdefault("ndim", ub.ndim)
+    return gad.deconvolve(_to_gpu(ub), gamma, space="spectral", **kw)
+
+
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((96, 128), 0.1), ((256, 256), 0.01),
+                                         ((32, 32, 32), 0.1), ((24, 48, 32), 0.1), ((48, 36, 24), 0.1)])
+@pytest.mark.parametrize("npass", [1, 5])
+def test_fixed_passes_f32(gad, method, shape, gamma, npass):
+    _, ub = _problem(shape, 3, gamma)
+    res = _solve(gad, ub, gamma, method=method, tol=0.0, maxit=npass)
+    assert int(res.iterations[0]) == npass and int(res.status[0]) == gad.AD_MAXIT
+    u64 = ub.astype(np.float64)
+    if npass == 1:
+        ref = oracle.solve(method, u64, gamma, tol=0.0, maxit=1)
+        assert _rel(res.u.double().cpu().numpy(), ref.u) < 1e-5
+        np.testing.assert_allclose(res.history[0, :2], ref.history, rtol=1e-5)
+        return
+    base, runs = ensemble_runs(method, u64, gamma, 0.0, npass, "f32")
+    tol, spread = field_tolerance(base, runs, "f32")
+    assert _rel(res.u.double().cpu().numpy(), base.u) < tol, spread
+    np.testing.assert_allclose(res.history[0, :npass + 1], base.history,
+                               rtol=history_tolerance(base, runs, 1e-5))
+
+
+# gamma = 0.01 is compared at 5 passes and to tolerance (below), not at 20
+# fixed passes: there (condition number 2e4) equally valid float32 runs of
+# BiCGSTAB drift apart by 15% after 20 passes and a single residual spike
+# decides where a run stands, so the fixed-pass field says nothing about
+# correctness; the tolerance-stopped solve is checked against the exact
+# inverse with a rigorous bound instead.
+@pytest.mark.parametrize("method", METHODS)
+@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((128, 96), 0.1), ((32, 32, 32), 0.1)])
+def test_twenty_passes_f32(gad, method, shape, gamma):
+    _, ub = _problem(shape, 3, gamma)
+    res = _solve(gad, ub, gamma, method=method, tol=0.0, maxit=20)
+    base, runs = ensemble_runs(method, ub.astype(np.float64), gamma, 0.0, 20, "f32")
+    tol, spread = field_tolerance(base, runs, "f32")
+    assert _rel(res.u.double().cpu().numpy(), base.u) < tol, spread
+
+
+def test_van_cittert_closed_form_f32(gad):
+    """Van Cittert on the spectrum is mode by mode u_N = (1 - (1 - G_hat)^(N+1)) / G_hat u_bar_hat:
+    no Krylov scalars, so float32 stays within 1e-5 of the closed form at every N."""
+    gamma, shape = 0.1, (64, 96)
+    u, ub = _problem(shape, 7, gamma)
+    gh = oracle.transfer_function(shape, gamma)
+    ubh = np.fft.fftn(ub.astype(np.float64))
+    for n in (1, 7, 20):
+        res = _solve(gad, ub, gamma, method="vancittert", tol=0.0, maxit=n)
+        ref = np.real(np.fft.ifftn(ubh * (1.0 - (1.0 - gh) ** (n + 1)) / gh))
+        assert _rel(res.u.double().cpu().numpy(), ref) < 1e-5, n
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_fixed_passes_f64(gad, method):
+    _, ub = _problem((128, 128), 0, 0.1, dtype=np.float64)
+    for npass in (1, 5, 20):
+        res = _solve(gad, ub, 0.1, method=method, tol=0.0, maxit=npass)
+        base, runs = ensemble_runs(method, ub, 0.1, 0.0, npass, "f64")
+        tol, spread = field_tolerance(base, runs, "f64")
+        if npass == 1:
+            tol = 1e-12
+        assert _rel(res.u.cpu().numpy(), base.u) < tol, (npass, spread)
+        np.testing.assert_allclose(res.history[0, :npass + 1], base.history,
+                                   rtol=history_tolerance(base, runs, 1e-11))
+
+
+@pytest.mark.parametrize("method", METHODS)
+def test_config1_f64_to_tolerance(gad, method):
+    """128^2 float64 vorticity, gamma = 0.1, to relative residual 1e-10."""
+    spec = lambda k: fields.spectrum_2d_kraichnan(k, kp=8.0)
+    u = fields.random_scalar_field((128, 128), 0, spec)
+    ub = oracle.filter_field(u, 0.1)
+    maxit = 5000 if method in ("vancittert", "sd") else 1000
+    res = _solve(gad, ub, 0.1, method=method, tol=1e-10, maxit=maxit, true_residual=True)
+    base, runs = ensemble_runs(method, ub, 0.1, 1e-10, maxit, "f64")
+    assert int(res.status[0]) == gad.AD_OK == base.status
+    ok, counts = count_ok(int(res.iterations[0]), base, runs)
+    assert ok, (int(res.iterations[0]), counts)
+    tol, spread = field_tolerance(base, runs, "f64")
+    assert _rel(res.u.cpu().numpy(), base.u) < tol, spread
+    assert _rel(res.u.cpu().numpy(), oracle.exact_inverse(ub, 0.1)) < 1e-7
+    assert res.history[0, int(res.iterations[0])] <= 1e-10
+    assert res.true_residual[0] < 2e-10
+
+
+@pytest.mark.parametrize("method", ["cg", "bicgstab"])
+@pytest.mark.parametrize("shape,gamma", [((256, 256), 0.1), ((512, 512), 0.01), ((64, 64, 64), 0.1)])
+def test_f32_to_tolerance_counts(gad, method, shape, gamma):
+    _, ub = _problem(shape, 1, gamma)
+    tol = 1e-6
+    res = _solve(gad, ub, gamma, method=method, tol=tol, maxit=2000, true_residual=True)
+    base, runs = ensemble_runs(method, ub.astype(np.float64), gamma, tol, 2000, "f32")
+    n_gpu = int(res.iterations[0])
+    assert int(res.status[0]) == gad.AD_OK
+    ok, counts = count_ok(n_gpu, base, runs)
+    assert ok, (n_gpu, counts)
+    assert res.history[0, n_gpu] <= tol
+    assert res.true_residual[0] < 20 * tol
+    # against the exact (Fourier) inverse: ||u - u_ex|| <= ||r_true|| / G_hat_min
+    u64 = ub.astype(np.float64)
+    uex = oracle.exact_inverse(u64, gamma)
+    ref = np.linalg.norm(u64 - oracle.filter_field(u64, gamma))
+    gmin = oracle.transfer_function(shape, gamma).min()
+    assert np.linalg.norm(res.u.double().cpu().numpy() - uex) <= 1.05 * res.true_residual[0] * ref / gmin
+
+
+def test_edge_cases_per_field_status(gad):
+    """Regular, zero, constant and NaN fields in one batch; the regular
+    field's result is bitwise the same as when it is solved alone."""
+    n = 64
+    _, ub = _problem((n, n), 2, 0.1)
+    batch = np.stack([ub, np.zeros_like(ub), np.full_like(ub, 2.5), ub.copy()])
+    batch[3, 5, 7] = np.nan
+    for method in METHODS:
+        res = _solve(gad, batch, 0.1, method=method, tol=1e-5, maxit=3000, ndim=2)
+        alone = _solve(gad, ub, 0.1, method=method, tol=1e-5, maxit=3000)
+        assert int(res.status[0]) == gad.AD_OK and res.iterations[0] == alone.iterations[0]
+        np.testing.assert_array_equal(res.u[0].cpu().numpy(), alone.u.cpu().numpy())
+        assert res.history[0, res.iterations[0]] <= 1e-5
+        assert int(res.status[1]) == gad.AD_OK and int(res.iterations[1]) == 0
+        assert int(res.status[2]) == gad.AD_OK and int(res.iterations[2]) == 0
+        assert int(res.status[3]) == gad.AD_ERR_NONFINITE
+        np.testing.assert_array_equal(res.u[1].cpu().numpy(), 0.0)
+        np.testing.assert_allclose(res.u[2].cpu().numpy(), 2.5, rtol=1e-6)
+
+
+def test_maxit_zero_round_trip_and_single_mode(gad):
+    _, ub = _problem((32, 48), 4, 0.1)
+    res = _solve(gad, ub, 0.1, method="cg", tol=1e-6, maxit=0)
+    assert int(res.status[0]) == gad.AD_MAXIT and int(res.iterations[0]) == 0
+    assert _rel(res.u.double().cpu().numpy(), ub.astype(np.float64)) < 1e-6   # one transform round trip
+    n = 64
+    x = 2 * np.pi * np.arange(n) / n
+    X, Y = np.meshgrid(x, x)
+    u = np.cos(3 * X + 5 * Y)
+    ub1 = oracle.filter_field(u, 0.2)
+    for method in ("sd", "cg", "bicgstab"):
+        r = _solve(gad, ub1, 0.2, method=method, tol=1e-10, maxit=10)
+        assert int(r.iterations[0]) == 1 and int(r.status[0]) == gad.AD_OK, method
+        np.testing.assert_allclose(r.u.cpu().numpy(), u, atol=1e-12)
+
+
+def test_initial_guess_f64(gad):
+    u, ub = _problem((96, 96), 5, 0.1, dtype=np.float64)
+    u0 = 0.5 * (ub + u)
+    res = _solve(gad, ub, 0.1, method="bicgstab", tol=1e-9, maxit=500, u0=_to_gpu(u0))
+    base, runs = ensemble_runs("bicgstab", ub, 0.1, 1e-9, 500, "f64", u0=u0)
+    ok, counts = count_ok(int(res.iterations[0]), base, runs)
+    assert ok, (int(res.iterations[0]), counts)
+    assert res.history[0, 0] == pytest.approx(base.history[0], rel=1e-12)
+    assert res.history[0, int(res.iterations[0])] <= 1e-9
+    res1 = _solve(gad, ub, 0.1, method="bicgstab", tol=0.0, maxit=1, u0=_to_gpu(u0))
+    ref1 = oracle.bicgstab(ub, 0.1, tol=0.0, maxit=1, u0=u0)
+    assert _rel(res1.u.cpu().numpy(), ref1.u) < 1e-12
+    np.testing.assert_allclose(res1.history[0], ref1.history, rtol=1e-11)
+
+
+def test_physical_and_spectral_space_agree_f64(gad):
+    """Float64, solved to 1e-9 in both iteration spaces: Van Cittert (no
+    Krylov scalars) needs the same number of passes; CG and BiCGSTAB agree
+    within max(3, 10%) (finite-precision loss of orthogonality delays them
+    by amounts that depend on the rounding pattern, which differs between
+    the spaces); steepest descent may settle into another zigzag regime.
+    The two solutions differ by at most (||r_a|| + ||r_b||)/G_hat_min."""
+    shape, gamma = (96, 128), 0.1
+    _, ub = _problem(shape, 9, gamma, dtype=np.float64)
+    t = _to_gpu(ub)
+    ref = np.linalg.norm(ub - oracle.filter_field(ub, gamma))
+    gmin = oracle.transfer_function(shape, gamma).min()
+    for method in METHODS:
+        maxit = 5000 if method in ("vancittert", "sd") else 1000
+        a = gad.deconvolve(t, gamma, method=method, tol=1e-9, maxit=maxit, true_residual=True)
+        b = gad.deconvolve(t, gamma, method=method, tol=1e-9, maxit=maxit, true_residual=True, space="spectral")
+        assert int(a.status[0]) == int(b.status[0]) == gad.AD_OK, method
+        na, nb = int(a.iterations[0]), int(b.iterations[0])
+        if method == "vancittert":
+            assert na == nb
+        elif method != "sd":
+            assert abs(na - nb) <= max(3, 0.1 * na), (method, na, nb)
+        bound = (a.true_residual[0] + b.true_residual[0]) * ref / gmin
+        assert np.linalg.norm(a.u.cpu().numpy() - b.u.cpu().numpy()) <= 1.01 * bound, method
+
+
+def test_graph_and_host_loop_agree(gad):
+    _, ub = _problem((128, 96), 6, 0.1)
+    for method in METHODS:
+        gad.set_graph_mode(True)
+        a = _solve(gad, ub, 0.1, method=method, tol=1e-6, maxit=3000)
+        gad.set_graph_mode(False)
+        b = _solve(gad, ub, 0.1, method=method, tol=1e-6, maxit=3000)
+        gad.set_graph_mode(True)
+        assert int(a.iterations[0]) == int(b.iterations[0])
+        np.testing.assert_array_equal(a.u.cpu().numpy(), b.u.cpu().numpy())
+
+
+def test_batched_uneven_matches_single_solves(gad):
+    shapes = [(64, 64), (96, 128), (32, 32, 32), (64, 64), (24, 48, 32)]
+    ubs, gammas = [], []
+    for i, sh in enumerate(shapes):
+        _, ub = _problem(sh, 20 + i, 0.1)
+        ubs.append(ub)
+        gammas.append(0.1)
+    outs, its, sts, _ = gad.deconvolve_batched([_to_gpu(u) for u in ubs], gammas, method="bicgstab", tol=1e-6,
+                                               maxit=2000, space="spectral")
+    assert np.all(sts == gad.AD_OK)
+    for i, ub in enumerate(ubs):
+        alone = _solve(gad, ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000)
+        assert int(its[i]) == int(alone.iterations[0])
+        np.testing.assert_array_equal(outs[i].cpu().numpy(), alone.u.cpu().numpy())
+
+
+def test_bench_workload_full_size(gad):
+    """16 x 2048^2 float32, gamma = 0.01, tolerance 1e-6 (the benchmark's
+    launch configuration): every field converges, the true residual tracks
+    the recurrence, and 3 fixed passes match the oracle on one field."""
+    spec = lambda k: fields.spectrum_2d_kraichnan(k, kp=10.0, kcut=600.0)
+    batch, n = 16, 2048
+    ub = np.empty((batch, n, n), dtype=np.float32)
+    for b in range(batch):
+        ub[b] = oracle.filter_field(fields.random_scalar_field((n, n), b, spec), 0.01)
+    t = _to_gpu(ub)
+    for method in ("cg", "bicgstab"):
+        res = gad.deconvolve(t, 0.01, method=method, tol=1e-6, maxit=3000, true_residual=True, ndim=2,
+                             space="spectral")
+        assert np.all(res.status == gad.AD_OK), res.status
+        assert np.all(res.true_residual < 50e-6)
+        for b in range(batch):
+            assert res.history[b, res.iterations[b]] <= 1e-6
+    res = gad.deconvolve(t, 0.01, method="bicgstab", tol=0.0, maxit=3, ndim=2, space="spectral")
+    ref = oracle.bicgstab(ub[5].astype(np.float64), 0.01, tol=0.0, maxit=3, precision="f32")
+    assert _rel(res.u[5].double().cpu().numpy(), ref.u) < 1e-5
+
+
+def test_autotuned_launch_width(gad):
+    """The autotuner picks the spectral passes' blocks per field; the tuned
+    plan still converges to the same tolerance with a true residual that
+    tracks the recurrence."""
+    shape, gamma = (256, 384), 0.1
+    ub = np.stack([_problem(shape, 30 + i, gamma)[1] for i in range(2)])
+    before = _solve(gad, ub, gamma, method="bicgstab", tol=1e-6, maxit=2000, ndim=2, true_residual=True)
+    gad.autotune(shape, gamma, batch=2, method="bicgstab", space="spectral")
+    after = _solve(gad, ub, gamma, method="bicgstab", tol=1e-6, maxit=2000, ndim=2, true_residual=True)
+    assert np.all(after.status == gad.AD_OK) and np.all(after.true_residual < 20e-6)
+    assert np.all(np.abs(after.iterations - before.iterations) <= 3)
