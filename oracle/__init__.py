@@ -14,6 +14,8 @@ Contents
                   conjugate gradient (Algorithm 3) and BiCGSTAB (Algorithm 4)
                   for G u = u_bar (Eq. tau3), with the stopping and
                   breakdown rules stated in solvers.py.
+  precond.py   -- preconditioned CG with a periodic finite-difference
+                  approximation of G^{-1} (no counterpart in the paper).
 
 Parity status: every function here is pinned by the tests under
 tests/test_oracle_*.py (closed forms, hand-computed transfer values,
@@ -40,4 +42,10 @@ from .solvers import (  # noqa: F401
     STATUS_MAXIT,
     STATUS_BREAKDOWN,
     STATUS_NONFINITE,
+)
+from .precond import (  # noqa: F401
+    stencil_coefficients,
+    apply_preconditioner,
+    preconditioner_symbol,
+    preconditioned_cg,
 )

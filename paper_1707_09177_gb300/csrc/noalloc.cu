@@ -189,6 +189,7 @@ ad_status run_static(const ad_grid* g, const void* in, void* out, int batch, cud
   ok = ok && plan_s(Lf, Lf, 0, cs, g->ndim == 3 ? (const void*)twz : (const void*)twy, Lf, true, fl);
   if (g->ndim == 3) ok = ok && plan_s(ny, ny, pow2_part_s(nz), cs, twy, ny, false, yf);
   if (!ok) return AD_ERR_ARG;
+  xf.rcp_a = 1.0f / (float)(nx / 4);
   xf.rcp_b = 1.0f / (float)(M / 2 + 1);
   xf.grid = dim3(ny * nz / xf.W, batch);
   fl.grid = dim3((nseq + fl.W - 1) / fl.W, batch);

@@ -304,12 +304,269 @@ template <typename T> __device__ __forceinline__ void st2(T* p, T a, T b) {
 // x and y passes fit 80 registers at E = 16 (3 blocks of 256 per SM); the filter
 // pass keeps two FFT stages' worth of state live and gets 128.
 #define GAD_BOUNDS(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 3 : 2)
-#define GAD_BOUNDS_FILT __launch_bounds__(256, 2)
+#define GAD_BOUNDS_FILT(T, E) __launch_bounds__(256, 2)
 
-// Forward x pass: the Krylov prologue is fused into the first FFT stage,
-// which reads the packed rows z[n] = x[2n] + i x[2n+1] straight from global
-// memory; the real-to-complex split and the transposed store to S1 follow.
-//   rcp_b = 1/(nx/4 + 1)
+// ---------------------------------------------------------------------------
+// Row-tile streaming for the fused Krylov prologue/epilogue of the x passes.
+//
+// A block of an x pass owns W consecutive grid rows, i.e. one contiguous run
+// of W*nx reals in every field vector. The vector updates are streamed over
+// that run in chunks of four reals (one float4), U chunks per thread with all
+// their loads issued before any store, so each thread keeps U x (vectors
+// read) 16-byte loads in flight. Chunk c of row w holds the packed complex
+// elements 2q, 2q+1 (q = c mod nx/4) of the tile's shared-memory row.
+
+// L2 prefetch of a contiguous range (16-byte aligned, multiple of 16 bytes),
+// split into 16 KiB bulk requests issued by the first threads of the block.
+__device__ __forceinline__ void prefetch_l2(const void* p, long long bytes, int tid, int nthr) {
+  const long long chunk = 16384;
+  const long long n = (bytes + chunk - 1) / chunk;
+  for (long long i = tid; i < n; i += nthr) {
+    const long long off = i * chunk;
+    const unsigned sz = (unsigned)min(chunk, bytes - off);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"((const char*)p + off), "r"(sz) : "memory");
+  }
+}
+
+template <int U, class Ld, class Fin>
+__device__ __forceinline__ void stream_tile(int W, int nx, float rcp_q, long long base, int tid, int nthr, Ld& ld,
+                                            Fin& fin) {
+  const int qn = nx >> 2;
+  const int total = W * qn;
+  for (int c0 = tid; c0 < total; c0 += nthr * U) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = c0 + u * nthr;
+      if (c < total) {
+        const int w = fquot(c, rcp_q);
+        ld(u, base + (long long)w * nx + 4 * (c - w * qn));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int c = c0 + u * nthr;
+      if (c < total) {
+        const int w = fquot(c, rcp_q);
+        const int q = c - w * qn;
+        fin(u, w, q, base + (long long)w * nx + 4 * q);
+      }
+    }
+  }
+}
+
+template <typename T> __device__ __forceinline__ void put_pair(typename cpx<T>::t* row, int q, const V4<T>& x) {
+  using C = typename cpx<T>::t;
+  row[phys(2 * q)] = C{x.v[0], x.v[1]};
+  row[phys(2 * q + 1)] = C{x.v[2], x.v[3]};
+}
+template <typename T> __device__ __forceinline__ V4<T> get_pair(const typename cpx<T>::t* row, int q) {
+  const auto a = row[phys(2 * q)], b = row[phys(2 * q + 1)];
+  return {{a.x, a.y, b.x, b.y}};
+}
+
+// x = prologue of the forward x pass for the block's row tile, written into
+// the shared-memory rows as packed complex (z[n] = x[2n] + i x[2n+1]).
+template <typename T, int U>
+__device__ __forceinline__ void xfwd_prologue(const PassArgs<T>& a, typename cpx<T>::t* s, long long base, bool first,
+                                              T al, T be, T om, int tid, int nthr) {
+  const T* __restrict__ vA = a.A;
+  const T* __restrict__ vB = a.B;
+  T* __restrict__ vO1 = a.O1;
+  T* __restrict__ vO2 = a.O2;
+  T* __restrict__ vO3 = a.O3;
+  const int ld = a.ld, W = a.W, nx = a.nx;
+  const float rq = a.rcp_a;
+  V4<T> r_[U], x_[U], y_[U];
+  switch (a.op) {
+    case XF_VC: {                                 // U += R; x = R
+      auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); x_[u] = ld4(vO1 + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        V4<T> o;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) o.v[e] = x_[u].v[e] + r_[u].v[e];
+        st4(vO1 + g, o);
+        put_pair<T>(s + w * ld, q, r_[u]);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XF_CG: {                                 // U += alpha P; P = R + beta P (first pass: P = R)
+      if (first) {
+        auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); };
+        auto fin = [&](int u, int w, int q, long long g) { st4(vO2 + g, r_[u]); put_pair<T>(s + w * ld, q, r_[u]); };
+        stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      } else {
+        auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); x_[u] = ld4(vO2 + g); y_[u] = ld4(vO1 + g); };
+        auto fin = [&](int u, int w, int q, long long g) {
+          V4<T> uo, po;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            uo.v[e] = fma(al, x_[u].v[e], y_[u].v[e]);
+            po.v[e] = fma(be, x_[u].v[e], r_[u].v[e]);
+          }
+          st4(vO1 + g, uo);
+          st4(vO2 + g, po);
+          put_pair<T>(s + w * ld, q, po);
+        };
+        stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      }
+      break;
+    }
+    case XF_BI_P: {                               // P = R + beta (P - omega Q) (first pass: P = R)
+      if (first) {
+        auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); };
+        auto fin = [&](int u, int w, int q, long long g) { st4(vO2 + g, r_[u]); put_pair<T>(s + w * ld, q, r_[u]); };
+        stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      } else {
+        auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); x_[u] = ld4(vO2 + g); y_[u] = ld4(vB + g); };
+        auto fin = [&](int u, int w, int q, long long g) {
+          V4<T> po;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) po.v[e] = fma(be, fma(-om, y_[u].v[e], x_[u].v[e]), r_[u].v[e]);
+          st4(vO2 + g, po);
+          put_pair<T>(s + w * ld, q, po);
+        };
+        stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      }
+      break;
+    }
+    case XF_BI_S: {                               // S = R - alpha Q
+      auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); y_[u] = ld4(vB + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        V4<T> so;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) so.v[e] = fma(-al, y_[u].v[e], r_[u].v[e]);
+        st4(vO3 + g, so);
+        put_pair<T>(s + w * ld, q, so);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    default: {                                    // XF_COPY: x = A (and O1 = A)
+      auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        if (vO1) st4(vO1 + g, r_[u]);
+        put_pair<T>(s + w * ld, q, r_[u]);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+  }
+}
+
+// Epilogue of the inverse x pass: y = G x sits in the shared-memory rows
+// (packed, y[2n] + i y[2n+1]); the vector updates and dots of the algorithm
+// are streamed over the block's row tile.
+template <typename T, int U>
+__device__ __forceinline__ void xinv_epilogue(const PassArgs<T>& a, const typename cpx<T>::t* s, long long base, T al,
+                                              T om, Acc<T>& acc0, Acc<T>& acc1, int tid, int nthr) {
+  const T* __restrict__ vA = a.A;
+  const T* __restrict__ vB = a.B;
+  const T* __restrict__ vC = a.C;
+  T* __restrict__ vO1 = a.O1;
+  T* __restrict__ vO2 = a.O2;
+  const int ld = a.ld, W = a.W, nx = a.nx;
+  const float rq = a.rcp_a;
+  V4<T> a_[U], b_[U], c_[U], d_[U];
+  switch (a.op) {
+    case XI_STORE: {
+      auto ldf = [&](int, long long) {};
+      auto fin = [&](int, int w, int q, long long g) { st4(vO1 + g, get_pair<T>(s + w * ld, q)); };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XI_INIT:                                 // r = A - y -> O1 (R), O2 (F0, optional); (r, r)
+    case XI_RES: {                                // res = A - y; (res, res)
+      const bool store = a.op == XI_INIT;
+      auto ldf = [&](int u, long long g) { a_[u] = ld4(vA + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        const V4<T> y = get_pair<T>(s + w * ld, q);
+        V4<T> r;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { r.v[e] = a_[u].v[e] - y.v[e]; acc0.add_prod(r.v[e], r.v[e]); }
+        if (store) {
+          st4(vO1 + g, r);
+          if (vO2) st4(vO2 + g, r);
+        }
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XI_VC:                                   // R -= y; (R, R)
+    case XI_CG: {                                 // R -= alpha y; (R, R)
+      const bool vc = a.op == XI_VC;
+      auto ldf = [&](int u, long long g) { a_[u] = ld4(vO1 + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        const V4<T> y = get_pair<T>(s + w * ld, q);
+        V4<T> r;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          r.v[e] = vc ? a_[u].v[e] - y.v[e] : fma(-al, y.v[e], a_[u].v[e]);
+          acc0.add_prod(r.v[e], r.v[e]);
+        }
+        st4(vO1 + g, r);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XI_SD: {                                 // U += alpha R; R -= alpha y; (R, R)
+      auto ldf = [&](int u, long long g) { a_[u] = ld4(vO1 + g); b_[u] = ld4(vO2 + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        const V4<T> y = get_pair<T>(s + w * ld, q);
+        V4<T> r, uo;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          uo.v[e] = fma(al, a_[u].v[e], b_[u].v[e]);
+          r.v[e] = fma(-al, y.v[e], a_[u].v[e]);
+          acc0.add_prod(r.v[e], r.v[e]);
+        }
+        st4(vO2 + g, uo);
+        st4(vO1 + g, r);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XI_BI_Q: {                               // Q = y; (F0, Q)
+      auto ldf = [&](int u, long long g) { a_[u] = ld4(vA + g); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        const V4<T> y = get_pair<T>(s + w * ld, q);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc0.add_prod(a_[u].v[e], y.v[e]);
+        st4(vO1 + g, y);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XI_BI_T: {          // t = y; U += alpha P + omega S; R = S - omega t; (R, R), (F0, R)
+      auto ldf = [&](int u, long long g) {
+        a_[u] = ld4(vA + g); b_[u] = ld4(vB + g); c_[u] = ld4(vC + g); d_[u] = ld4(vO1 + g);
+      };
+      auto fin = [&](int u, int w, int q, long long g) {
+        const V4<T> y = get_pair<T>(s + w * ld, q);
+        V4<T> r, uo;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          uo.v[e] = fma(om, c_[u].v[e], fma(al, b_[u].v[e], d_[u].v[e]));
+          r.v[e] = fma(-om, y.v[e], c_[u].v[e]);
+          acc0.add_prod(r.v[e], r.v[e]);
+          acc1.add_prod(a_[u].v[e], r.v[e]);
+        }
+        st4(vO1 + g, uo);
+        st4(vO2 + g, r);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Forward x pass: the Krylov prologue streams the block's row tile into the
+// shared-memory rows as packed complex (z[n] = x[2n] + i x[2n+1]); the
+// half-length FFT runs in shared memory, followed by the real-to-complex
+// split and the transposed store to S1.
+//   rcp_a = 1/(nx/4), rcp_b = 1/(nx/4 + 1)
 template <typename T, int E>
 __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   using C = typename cpx<T>::t;
@@ -326,64 +583,20 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   const long long base = (long long)f * a.P + (long long)row0 * nx;
   const bool first = st ? (st->iter == 0) : true;
   const T al = st ? T(st->alpha) : T(0), be = st ? T(st->beta) : T(0), om = st ? T(st->omega) : T(0);
-  const int op = a.op;
-  const T* __restrict__ vA = a.A;
-  const T* __restrict__ vB = a.B;
-  T* vO1 = a.O1;
-  T* vO2 = a.O2;
-  T* vO3 = a.O3;
-
-  auto load = [&](int w, int n) -> C {
-    const long long g = base + (long long)w * nx + 2 * n;
-    T x0, x1;
-    switch (op) {
-      case XF_VC: {                               // U += R; x = R
-        const V2<T> r = ld2(vA + g), u = ld2(vO1 + g);
-        st2(vO1 + g, u.x + r.x, u.y + r.y);
-        x0 = r.x; x1 = r.y;
-        break;
-      }
-      case XF_CG: {                               // U += alpha P; P = R + beta P
-        const V2<T> r = ld2(vA + g);
-        if (first) {
-          x0 = r.x; x1 = r.y;
-        } else {
-          const V2<T> p = ld2(vO2 + g), u = ld2(vO1 + g);
-          st2(vO1 + g, fma(al, p.x, u.x), fma(al, p.y, u.y));
-          x0 = fma(be, p.x, r.x); x1 = fma(be, p.y, r.y);
-        }
-        st2(vO2 + g, x0, x1);
-        break;
-      }
-      case XF_BI_P: {                             // P = R + beta (P - omega Q)
-        const V2<T> r = ld2(vA + g);
-        if (first) {
-          x0 = r.x; x1 = r.y;
-        } else {
-          const V2<T> p = ld2(vO2 + g), q = ld2(vB + g);
-          x0 = fma(be, fma(-om, q.x, p.x), r.x);
-          x1 = fma(be, fma(-om, q.y, p.y), r.y);
-        }
-        st2(vO2 + g, x0, x1);
-        break;
-      }
-      case XF_BI_S: {                             // S = R - alpha Q
-        const V2<T> r = ld2(vA + g), q = ld2(vB + g);
-        x0 = fma(-al, q.x, r.x); x1 = fma(-al, q.y, r.y);
-        st2(vO3 + g, x0, x1);
-        break;
-      }
-      default: {                                  // XF_COPY: x = A (and O1 = A)
-        const V2<T> v = ld2(vA + g);
-        if (vO1) st2(vO1 + g, v.x, v.y);
-        x0 = v.x; x1 = v.y;
-        break;
-      }
-    }
-    return C{x0, x1};
-  };
+  {
+    // the vectors the prologue reads, fetched into L2 as whole tiles so that
+    // only the first of the streaming rounds waits on DRAM
+    const long long tb = (long long)a.W * nx * sizeof(T);
+    const int op = a.op;
+    prefetch_l2(a.A + base, tb, tid, nthr);
+    if (op == XF_VC || (op == XF_CG && !first)) prefetch_l2(a.O1 + base, tb, tid, nthr);
+    if ((op == XF_CG || op == XF_BI_P) && !first) prefetch_l2(a.O2 + base, tb, tid, nthr);
+    if ((op == XF_BI_P && !first) || op == XF_BI_S) prefetch_l2(a.B + base, tb, tid, nthr);
+  }
+  xfwd_prologue<T, 2>(a, s, base, first, al, be, om, tid, nthr);
+  __syncthreads();
   SmemRows<C> rows{s, a.ld};
-  fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true);
+  fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
   // split the packed half-length transform into the real-input spectrum
   const C* twx = reinterpret_cast<const C*>(a.twx);
   const int h1 = (M >> 1) + 1;
@@ -410,7 +623,8 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
 }
 
 // Inverse x pass: transposed load from S1, complex-to-real preparation, FFT
-// whose last stage writes the rows through the fused epilogue and dots.
+// in shared memory, then the fused epilogue and dots streamed over the row
+// tile.
 template <typename T, int E>
 __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
   using C = typename cpx<T>::t;
@@ -426,6 +640,19 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
   const int z = row0 / a.ny, y0 = row0 - z * a.ny;
   Acc<T> acc[3];
   if (act) {
+    const long long base = (long long)f * a.P + (long long)row0 * nx;
+    {
+      // the epilogue's input vectors, fetched into L2 while the FFT runs
+      const long long tb = (long long)a.W * nx * sizeof(T);
+      const int op = a.op;
+      if (op == XI_INIT || op == XI_RES || op == XI_BI_Q || op == XI_BI_T) prefetch_l2(a.A + base, tb, tid, nthr);
+      if (op == XI_VC || op == XI_CG || op == XI_SD || op == XI_BI_T) prefetch_l2(a.O1 + base, tb, tid, nthr);
+      if (op == XI_SD) prefetch_l2(a.O2 + base, tb, tid, nthr);
+      if (op == XI_BI_T) {
+        prefetch_l2(a.B + base, tb, tid, nthr);
+        prefetch_l2(a.C + base, tb, tid, nthr);
+      }
+    }
     const C* S1 = reinterpret_cast<const C*>(a.S1) + (long long)f * a.SP + (long long)z * a.kxn * a.ny + y0;
     load_transposed<C, 8>(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
     __syncthreads();
@@ -448,78 +675,11 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
       }
     }
     __syncthreads();
-    const long long base = (long long)f * a.P + (long long)row0 * nx;
-    const T al = st ? T(st->alpha) : T(0), om = st ? T(st->omega) : T(0);
-    const int op = a.op;
-    const T* __restrict__ vA = a.A;
-    const T* __restrict__ vB = a.B;
-    const T* __restrict__ vC = a.C;
-    T* vO1 = a.O1;
-    T* vO2 = a.O2;
-    Acc<T> acc0, acc1;
-    auto emit = [&](int w, int n, const C& y) {
-      const long long g = base + (long long)w * nx + 2 * n;
-      switch (op) {
-        case XI_STORE:
-          st2(vO1 + g, y.x, y.y);
-          break;
-        case XI_INIT: {
-          const V2<T> u = ld2(vA + g);
-          const T r0 = u.x - y.x, r1 = u.y - y.y;
-          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
-          st2(vO1 + g, r0, r1);
-          if (vO2) st2(vO2 + g, r0, r1);
-          break;
-        }
-        case XI_RES: {
-          const V2<T> u = ld2(vA + g);
-          const T r0 = u.x - y.x, r1 = u.y - y.y;
-          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
-          break;
-        }
-        case XI_VC: {
-          const V2<T> r = ld2(vO1 + g);
-          const T r0 = r.x - y.x, r1 = r.y - y.y;
-          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
-          st2(vO1 + g, r0, r1);
-          break;
-        }
-        case XI_CG: {
-          const V2<T> r = ld2(vO1 + g);
-          const T r0 = fma(-al, y.x, r.x), r1 = fma(-al, y.y, r.y);
-          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
-          st2(vO1 + g, r0, r1);
-          break;
-        }
-        case XI_SD: {
-          const V2<T> r = ld2(vO1 + g), u = ld2(vO2 + g);
-          st2(vO2 + g, fma(al, r.x, u.x), fma(al, r.y, u.y));
-          const T r0 = fma(-al, y.x, r.x), r1 = fma(-al, y.y, r.y);
-          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
-          st2(vO1 + g, r0, r1);
-          break;
-        }
-        case XI_BI_Q: {
-          const V2<T> f0 = ld2(vA + g);
-          acc0.add_prod(f0.x, y.x); acc0.add_prod(f0.y, y.y);
-          st2(vO1 + g, y.x, y.y);
-          break;
-        }
-        case XI_BI_T: {
-          const V2<T> f0 = ld2(vA + g), p = ld2(vB + g), sv = ld2(vC + g), u = ld2(vO1 + g);
-          st2(vO1 + g, fma(om, sv.x, fma(al, p.x, u.x)), fma(om, sv.y, fma(al, p.y, u.y)));
-          const T r0 = fma(-om, y.x, sv.x), r1 = fma(-om, y.y, sv.y);
-          acc0.add_prod(r0, r0); acc0.add_prod(r1, r1);
-          acc1.add_prod(f0.x, r0); acc1.add_prod(f0.y, r1);
-          st2(vO2 + g, r0, r1);
-          break;
-        }
-        default:
-          break;
-      }
-    };
     SmemRows<C> rows{s, a.ld};
-    fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false);
+    fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
+    const T al = st ? T(st->alpha) : T(0), om = st ? T(st->omega) : T(0);
+    Acc<T> acc0, acc1;
+    xinv_epilogue<T, 2>(a, s, base, al, om, acc0, acc1, tid, nthr);
     acc[0] = acc0;
     acc[1] = acc1;
   }
@@ -532,7 +692,7 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
 // back. fft holds the forward plan, fft_inv the reversed one. In 3D the
 // sequence index is kx*ny + ky.
 template <typename T, int E>
-__global__ void GAD_BOUNDS_FILT k_filt(PassArgs<T> a) {
+__global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
