@@ -139,6 +139,8 @@ def _pass_bytes(kind, op, P, SP, B, method):
         return {0: 1, 1: 3, 2: 4, 3: 1, 4: 4, 5: 3, 6: 5, 7: 4, 8: 2, 9: 6}[op] * s
     if kind in ("lfwd", "linv"):
         return 2 * s
+    if kind == "sten":
+        return 2 * v                                   # r in, z = M r out
     if kind == "filt":
         return 2 * s                                   # spectrum in, filtered spectrum out
     if kind == "xfwd":
@@ -223,12 +225,18 @@ def _extra_workloads(gad, dev, extras):
         its = [int(x) for x in r.iterations]
         rs, ts = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3,
                                                space="spectral"))
+        rp, tp = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3))
         out["velocity3d_256_f32"] = {"mpoints_s": 3 * n ** 3 / t / 1e6, "ms": t * 1e3, "iterations": its,
                                      "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches,
                                      "spectral": {"mpoints_s": 3 * n ** 3 / ts / 1e6, "ms": ts * 1e3,
                                                   "iterations": [int(x) for x in rs.iterations],
-                                                  "converged": bool(np.all(rs.status == gad.AD_OK))}}
-        del ub, r
+                                                  "converged": bool(np.all(rs.status == gad.AD_OK))},
+                                     "pcg": {"mpoints_s": 3 * n ** 3 / tp / 1e6, "ms": tp * 1e3,
+                                             "iterations": [int(x) for x in rp.iterations],
+                                             "converged": bool(np.all(rp.status == gad.AD_OK))}}
+        if "closure" in extras:
+            out["closure_256"] = _closure_stats(gad, ub, r.u, n)
+        del ub, r, rp
         torch.cuda.empty_cache()
     if "uneven48" in extras:
         shapes = fields.uneven_batch(0)
@@ -260,6 +268,30 @@ def _extra_workloads(gad, dev, extras):
                                "one_call_per_group_mpoints_s": pts / t_seq / 1e6}
     if "learned512" in extras:
         out["velocity3d_512_f32_learned"] = _learned_512(gad, dev)
+    return out
+
+
+def _closure_stats(gad, ub, ustar, n):
+    """The step after the solve, on the 256^3 x 3 velocity: the sub-filter
+    stress tau_ij (6 pairs, one batched application of G), the energy
+    spectrum of u*, its vorticity and the histogram of omega_x (1000 bins
+    over +-6 sigma); each timed once after a warm-up."""
+    import torch
+    out = {}
+    ub, ustar = ub.reshape(1, 3, n, n, n).contiguous(), ustar.reshape(1, 3, n, n, n).contiguous()
+    tau, t = _timed(lambda: gad.closure(ub, ustar, 0.1, ncomp=3, ndim=3))
+    out["stress"] = {"ms": t * 1e3, "pairs": 6, "mpoints_s": 6 * n ** 3 / t / 1e6}
+    e, t = _timed(lambda: gad.spectrum(ustar, n, ncomp=3, ndim=3))
+    out["spectrum"] = {"ms": t * 1e3, "shells": n, "energy": float(e.sum())}
+    w, t = _timed(lambda: gad.curl(ustar, ndim=3))
+    out["curl"] = {"ms": t * 1e3}
+    wx = w[0, 0].contiguous()
+    sd = float(torch.std(wx))
+    h, t = _timed(lambda: gad.histogram(wx, -6 * sd, 6 * sd, 1000))
+    out["histogram"] = {"ms": t * 1e3, "bins": 1000, "gb_s": wx.numel() * 4 / t / 1e9,
+                        "outside": int(h[1] + h[2] + h[3])}
+    del tau, w, wx
+    torch.cuda.empty_cache()
     return out
 
 
@@ -319,6 +351,9 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
     gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=2, ndim=3, history=False, space="spectral")
     sp_plain, t_sp_plain = timed(lambda: solve(space="spectral"))
     sp_learned, t_sp_solve = timed(lambda: solve(u0, space="spectral"))
+    gad.deconvolve(ub, gamma, method="pcg", tol=1e-6, maxit=2, ndim=3, history=False)
+    pcg, t_pcg = timed(lambda: gad.deconvolve(ub, gamma, method="pcg", tol=1e-6, maxit=4000, ndim=3,
+                                              history=False))
     diff = float(torch.linalg.vector_norm(learned.u - plain.u) / torch.linalg.vector_norm(plain.u))
     pts = 3.0 * n ** 3
     t_learned = t_inf + t_solve
@@ -340,6 +375,9 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
                         "converged": bool(np.all(sp_learned.status == gad.AD_OK))},
             "wall_time_ratio_plain_over_learned": t_sp_plain / (t_inf + t_sp_solve)},
         "wall_time_ratio_plain_over_learned": t_plain / t_learned,
+        "preconditioned_cg": {"ms": t_pcg * 1e3, "mpoints_s": pts / t_pcg / 1e6,
+                              "iterations": [int(x) for x in pcg.iterations],
+                              "converged": bool(np.all(pcg.status == gad.AD_OK))},
         "rel_l2_learned_vs_plain_solution": diff,
         "train": {"pairs": npairs, "shape": [n_train] * 3, "epochs": epochs, "batch": batch, "lr": lr,
                   "seconds": t_train, "loss_per_epoch": [float(x) for x in hist],
@@ -396,8 +434,9 @@ def main():
     ap.add_argument("--space", default="physical", choices=["physical", "spectral"],
                     help="iteration space of the timed solve: physical (G by FFT passes every iteration, the "
                          "paper's formulation) or spectral (iterate on the half spectra, G pointwise)")
-    ap.add_argument("--extras", default="methods,3d256,uneven48,learned512",
-                    help="comma list of extra measurements on rank 0: methods, 3d256, uneven48, learned512")
+    ap.add_argument("--extras", default="methods,3d256,closure,uneven48,learned512",
+                    help="comma list of extra measurements on rank 0: methods, 3d256, closure (needs 3d256), "
+                         "uneven48, learned512")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -504,7 +543,7 @@ def main():
     if rank == 0 and "methods" in extras:
         # comparison methods on the same batch (one timed solve each)
         methods = {}
-        for m, mi, sp in (("cg", 3000, "physical"), ("bicgstab", 3000, "physical"),
+        for m, mi, sp in (("cg", 3000, "physical"), ("bicgstab", 3000, "physical"), ("pcg", 3000, "physical"),
                           ("vancittert", VC_MAXIT, "physical"), ("cg", 3000, "spectral"),
                           ("bicgstab", 3000, "spectral"), ("vancittert", VC_MAXIT, "spectral")):
             step(m, maxit=mi, space=sp)
@@ -549,6 +588,11 @@ def main():
         line["roofline"] = roofline(args.space)
         other = "spectral" if args.space == "physical" else "physical"
         line["roofline_" + other] = roofline(other)
+        # the preconditioned CG pass set, with its stencil kernel
+        pp = gad.time_passes(n, gamma, B, method="pcg", reps=20)
+        for p in pp:
+            p["gbs"] = _pass_bytes(p["kind"], p["op"], P, SP, B, "pcg") / (p["ms"] * 1e-3) / 1e9
+        line["passes_pcg"] = [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in pp]
 
         # the oracle on this host's cores, bounded sample
         os.environ["OMP_NUM_THREADS"] = "1"
@@ -563,7 +607,7 @@ def main():
                                            "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
                                            "extrapolated to the %d passes the GPU solve of that field needed"
                                            % (args.method, t0, sample_passes, per, n0))}
-    if rank == 0 and (extras & {"3d256", "uneven48", "learned512"}):
+    if rank == 0 and (extras & {"3d256", "closure", "uneven48", "learned512"}):
         del out, dev_in, host_out
         torch.cuda.empty_cache()
         line["workloads"] = _extra_workloads(gad, dev, extras)

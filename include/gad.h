@@ -66,7 +66,24 @@ typedef enum {
    * after it. Same iterates as the physical-space method in exact
    * arithmetic; in floating point the result differs by rounding. Accepted
    * by ad_deconvolve, ad_deconvolve_batched, ad_time_pass and ad_autotune. */
-  AD_SPECTRAL = 4
+  AD_SPECTRAL = 4,
+  /* Flag OR-ed into AD_CG (physical space only; any other combination is
+   * AD_ERR_ARG): preconditioned CG. The paper solves Eq. tau3 without a
+   * preconditioner; this flag adds the textbook preconditioned CG with M,
+   * the second-order periodic finite-difference version of the filter's
+   * differential inverse G^{-1} = I - delta^2 Laplacian (Section 4, Eq. df):
+   *   z = M r = r + sum_d c_d (2 r_i - r_{i+e_d} - r_{i-e_d}),
+   *   c_d = (delta/h_d)^2 = (N_d / (2 pi k_c))^2,
+   * evaluated in the field's precision as ((r + c_x d_x) + c_y d_y) + c_z d_z
+   * with d = (2 r - left) - right, each operation rounded once. M is
+   * symmetric positive definite and commutes with G; M G has its spectrum in
+   * [4/pi^2, 1], so the pass count no longer grows with |k|^2/k_c^2. Per
+   * pass: one stencil pass (z = M r, (r, z)) and one application of G with
+   * Algorithm 3's updates (p = z + beta p). Same stopping rules and history
+   * (unpreconditioned residual ||r_n|| / ||u_bar - G u_bar||); rho_n =
+   * (r_n, z_n) <= 0 or not finite is AD_BREAKDOWN. Accepted by
+   * ad_deconvolve, ad_deconvolve_batched and ad_time_pass. */
+  AD_PRECOND = 8
 } ad_method;
 
 typedef enum { AD_F32 = 0, AD_F64 = 1 } ad_dtype;
@@ -195,7 +212,8 @@ ad_status ad_autotune(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method met
  * active and no scalar update. `index` selects the launch within the
  * iteration body (0 .. count-1, in launch order); index = -1 only reports
  * the count. Outputs (host, may be NULL): ms_per_launch, kind (0 forward x,
- * 1 inverse x, 2 filter, 3 forward y, 4 inverse y), op (the fused
+ * 1 inverse x, 2 filter, 3 forward y, 4 inverse y, 5 last-axis forward,
+ * 6 last-axis inverse, 7 spectral-space pass, 8 preconditioner stencil), op (the fused
  * prologue/epilogue/dot code of that pass), count (launches per iteration).
  * Blocks the host until the timing completes. No counterpart in the paper:
  * it exists to relate measured kernel time to the HBM roofline. */
@@ -227,6 +245,68 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
  * streams or host threads) race on it and must be serialized.
  * Returns AD_OK, AD_ERR_ARG or AD_ERR_CUDA. */
 ad_status ad_filter_static(const ad_grid* grid, const void* in, void* out, int batch, void* stream);
+
+/* ---- Closure and statistics of deconvolved fields --------------------------
+ * What the deconvolved field is for in the paper: the sub-filter stress of
+ * the structural closure model (Section 3) and the energy spectra and
+ * vorticity PDFs by which recovered fields are assessed (Sections 4.1, 4.2).
+ * Velocities are stored component-major: velocity v, component c at field
+ * index v*ncomp + c of a contiguous batch (components along x, y[, z]). */
+
+/* Largest nbins of ad_spectrum and of ad_histogram. */
+#define AD_MAX_SHELLS 8192
+#define AD_MAX_HIST_BINS 16384
+
+/* Sub-filter stress of the approximate-deconvolution closure, Eq. fge3 with
+ * the unfiltered velocity replaced by its deconvolved estimate u*:
+ *   tau_ij = u_bar_i u_bar_j - G(u*_i u*_j),   i <= j,
+ * for nvel velocities of ncomp (1..3) components. With u* = u_bar this is the
+ * Layton-Lewandowski model (Eq. tau2); with the Van Cittert estimate of N
+ * passes it is the AD model of order N + 1 (Eq. tau3 and its second-order
+ * form). One application of G over nvel * ncomp(ncomp+1)/2 fields; the
+ * products are formed in the forward pass and the stress in the inverse one.
+ *   ubar, ustar  device, [nvel][ncomp][P], inputs
+ *   tau          device, [nvel][npairs][P] output, pairs ordered (0,0), (0,1),
+ *                ..., (0,ncomp-1), (1,1), ..., (ncomp-1,ncomp-1); must not
+ *                overlap the inputs
+ * Enqueued on `stream` (asynchronous). */
+ad_status ad_closure(ad_ctx* ctx, const ad_grid* grid, int nvel, int ncomp, const void* ubar, const void* ustar,
+                     void* tau, void* stream);
+
+/* Shell-summed energy spectrum of nfields fields taken in groups of ncomp
+ * (the components of one velocity, or ncomp = 1 for scalar fields):
+ *   E[g][k] = sum over the group's fields and over wavevectors k' with
+ *             shell(|k'|^2) = k of |u_hat(k')|^2 / 2,   u_hat = FFT(u)/P,
+ * for k = 0 .. nbins-1, where shell(m) is the nearest integer to sqrt(m),
+ * halves rounded down (the smallest k >= 0 with k^2 + k >= m); wavevectors
+ * of higher shells are not counted. sum_k E = mean(|u|^2)/2 (Parseval) when
+ * every shell is counted. The paper shows such spectra (Sections 4.1, 4.2)
+ * without stating a convention; this is the one used here.
+ *   u   device, [nfields][P] input;  E host double[nfields/ncomp][nbins]
+ * Accumulated in float64; the order of the per-shell additions is not fixed,
+ * so repeated calls agree to rounding, not bit for bit. Blocks until E is
+ * written. nbins <= AD_MAX_SHELLS. */
+ad_status ad_spectrum(ad_ctx* ctx, const ad_grid* grid, int nfields, int ncomp, const void* u, int nbins,
+                      double* E, void* stream);
+
+/* Value histogram for a PDF (the vorticity PDFs of Sections 4.1, 4.2): with
+ * scale = nbins/(hi - lo), value x falls in bin floor((x - lo) * scale),
+ * computed in the data's precision with lo and scale rounded to it and each
+ * operation rounded once.
+ *   x       device, n values of dtype
+ *   counts  host int64[nbins + 3]: the bins, then the number of values below
+ *           (bin < 0), above (bin >= nbins) and NaN
+ * The PDF is counts[b] / (n (hi - lo) / nbins). Exact integer counts.
+ * Blocks until counts is written. nbins <= AD_MAX_HIST_BINS; lo < hi finite. */
+ad_status ad_histogram(ad_ctx* ctx, ad_dtype dtype, int64_t n, const void* x, double lo, double hi, int nbins,
+                       int64_t* counts, void* stream);
+
+/* Vorticity by spectral differentiation (d/dx_d multiplies the Fourier
+ * coefficient by i k_d, zero at the Nyquist index), for nvel velocities:
+ *   2D: u [nvel][2][Ny][Nx] -> omega [nvel][Ny][Nx], omega = dv/dx - du/dy
+ *   3D: u [nvel][3][Nz][Ny][Nx] -> omega [nvel][3][...], omega = curl u
+ * Device pointers; omega must not overlap u. Enqueued on `stream`. */
+ad_status ad_curl(ad_ctx* ctx, const ad_grid* grid, int nvel, const void* u, void* omega, void* stream);
 
 /* Enables (1, default) or disables (0) capture of each solve into one CUDA
  * graph whose iteration loop is a device-side conditional while node. With 0

@@ -46,6 +46,7 @@ from .solvers import (  # noqa: F401
 from .precond import (  # noqa: F401
     stencil_coefficients,
     apply_preconditioner,
+    apply_preconditioner_f32,
     preconditioner_symbol,
     preconditioned_cg,
 )

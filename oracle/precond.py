@@ -25,6 +25,8 @@ out in full:
                   z_{n+1} = M r_{n+1}, rho_{n+1} = (r_{n+1}, z_{n+1}),
                   beta_n = rho_{n+1} / rho_n, p_{n+1} = z_{n+1} + beta_n p_n.
     With M = I these are exactly the steps of Algorithm 3.
+  * precision="f32" evaluates M in float32 as apply_preconditioner_f32
+    states (the other float32 rules are those of solvers.py).
   * Stopping, counting and normalisation follow the rules of solvers.py: the
     stop test uses the unpreconditioned recurrence residual,
     h_n = ||r_n|| / ||u_bar - G u_bar||; rho_n <= 0 or a non-finite scalar is a
@@ -58,6 +60,22 @@ def apply_preconditioner(x, gamma):
     return out
 
 
+def apply_preconditioner_f32(x, gamma):
+    """M x in float32 arithmetic, each operation rounded once, in the order
+    z = ((x + c_x d_x) + c_y d_y) + c_z d_z with d = (2 x - left) - right along
+    each axis (x = last array axis first) and c_d rounded to float32: the
+    evaluation order a float32 implementation of M uses, so that the
+    float32-storage mode of preconditioned_cg sees the same rounding."""
+    x = np.asarray(x, dtype=np.float32)
+    cs = stencil_coefficients(x.shape, gamma)
+    two = x + x
+    z = x.copy()
+    for axis in reversed(range(x.ndim)):
+        d = (two - np.roll(x, 1, axis=axis)) - np.roll(x, -1, axis=axis)
+        z = z + np.float32(cs[axis]) * d
+    return z.astype(np.float64)
+
+
 def preconditioner_symbol(shape, gamma):
     """M_hat(k) = 1 + sum_d 4 c_d sin^2(pi k_d / N_d) on the full FFT grid."""
     cs = stencil_coefficients(shape, gamma)
@@ -75,7 +93,12 @@ def preconditioned_cg(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", r
     ar = _Arith(precision)
     sp = _Physical(np.shape(ubar), gamma)
     ubar, ref, u, r = _start(ubar, gamma, u0, ar, sp)
-    M = (lambda x: apply_preconditioner(x, gamma)) if precond else (lambda x: np.asarray(x, dtype=np.float64))
+    if not precond:
+        M = lambda x: np.asarray(x, dtype=np.float64)          # noqa: E731
+    elif ar.f32:
+        M = lambda x: apply_preconditioner_f32(x, gamma)       # noqa: E731
+    else:
+        M = lambda x: apply_preconditioner(x, gamma)           # noqa: E731
     rr = sp.inner(r, r)
     status, h0 = _pre_loop(rr, ref, tol, maxit)
     hist = [h0]

@@ -27,8 +27,9 @@ _LIB_PATH = os.path.join(_HERE, "libgad.so")
 
 AD_OK, AD_MAXIT, AD_BREAKDOWN = 0, 1, 2
 AD_ERR_ARG, AD_ERR_NONFINITE, AD_ERR_CUDA, AD_ERR_TIMEOUT, AD_ERR_NOMEM = -1, -2, -3, -4, -5
-METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3}
 AD_SPECTRAL = 4                     # flag: iterate on the half spectra (G a pointwise multiply)
+AD_PRECOND = 8                      # flag on AD_CG: preconditioned CG (stencil approximation of G^-1)
+METHODS = {"vancittert": 0, "cg": 1, "bicgstab": 2, "sd": 3, "pcg": 1 | AD_PRECOND}
 SPACES = ("physical", "spectral")
 
 
@@ -44,8 +45,8 @@ AD_F32, AD_F64 = 0, 1
 EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvolve_batched", "ad_time_pass",
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
             "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
-            "ad_guess_train")
-PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec"}
+            "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl")
+PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec", 8: "sten"}
 
 
 class ad_grid(ctypes.Structure):
@@ -114,6 +115,14 @@ def load(path=None):
     lib.ad_status_str.restype = ctypes.c_char_p
     lib.ad_last_error.argtypes = [c_p]
     lib.ad_last_error.restype = ctypes.c_char_p
+    lib.ad_closure.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_p, c_p, c_p, c_p]
+    lib.ad_closure.restype = c_i
+    lib.ad_spectrum.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_p, c_i, c_p, c_p]
+    lib.ad_spectrum.restype = c_i
+    lib.ad_histogram.argtypes = [c_p, c_i, ctypes.c_int64, c_p, c_d, c_d, c_i, c_p, c_p]
+    lib.ad_histogram.restype = c_i
+    lib.ad_curl.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_p, c_p, c_p]
+    lib.ad_curl.restype = c_i
     _lib = lib
     return lib
 
@@ -378,3 +387,86 @@ def guess_train(weights, ubar, utrue, gamma, epochs=20, batch=8, lr=2e-5, seed=0
                             ctypes.c_void_p(hist.ctypes.data), _stream_ptr(stream))
     _check(st, ctx)
     return hist[: int(epochs)]
+
+
+# --- closure and statistics of deconvolved fields ---------------------------
+
+def _velocity_grid(u, ncomp, ndim, gamma=1.0):
+    """Grid of a [..., ncomp, *grid] tensor and the number of velocities."""
+    g, batch, shape = _grid(u, ndim, gamma)
+    if batch % ncomp != 0:
+        raise ValueError("the leading axes must hold a multiple of ncomp = %d fields" % ncomp)
+    return g, batch // ncomp, shape
+
+
+def closure(ubar, ustar, gamma, ncomp=None, ndim=None, out=None, stream=None):
+    """Sub-filter stress tau_ij = u_bar_i u_bar_j - G(u*_i u*_j), i <= j (Eq.
+    fge3 with the deconvolved estimate), for tensors shaped [..., ncomp, *grid]
+    (ncomp defaults to ndim). Returns [..., npairs, *grid]."""
+    import torch
+    lib = load()
+    ctx = context(ubar.device.index)
+    if ndim is None:
+        ndim = 3 if ubar.dim() >= 4 and ubar.shape[-4] == 3 else 2
+    ncomp = ndim if ncomp is None else int(ncomp)
+    if ustar.shape != ubar.shape or ustar.dtype != ubar.dtype or not ustar.is_contiguous():
+        raise ValueError("ustar must match ubar in shape, dtype and layout")
+    g, nvel, shape = _velocity_grid(ubar, ncomp, ndim, gamma)
+    npairs = ncomp * (ncomp + 1) // 2
+    lead = tuple(ubar.shape[:ubar.dim() - ndim - 1])
+    if out is None:
+        out = torch.empty(lead + (npairs,) + tuple(shape), dtype=ubar.dtype, device=ubar.device)
+    st = lib.ad_closure(ctx, ctypes.byref(g), nvel, ncomp, ctypes.c_void_p(ubar.data_ptr()),
+                        ctypes.c_void_p(ustar.data_ptr()), ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream))
+    _check(st, ctx)
+    return out
+
+
+def spectrum(u, nbins, ncomp=1, ndim=None, stream=None):
+    """Shell-summed energy spectrum E[g][k], k < nbins, of the fields of ``u``
+    taken in groups of ncomp (float64 numpy array [groups, nbins])."""
+    lib = load()
+    ctx = context(u.device.index)
+    g, batch, _ = _grid(u, ndim, 1.0)
+    if batch % ncomp != 0:
+        raise ValueError("number of fields must be a multiple of ncomp")
+    e = np.zeros((batch // ncomp, int(nbins)), dtype=np.float64)
+    st = lib.ad_spectrum(ctx, ctypes.byref(g), batch, int(ncomp), ctypes.c_void_p(u.data_ptr()), int(nbins),
+                         ctypes.c_void_p(e.ctypes.data), _stream_ptr(stream))
+    _check(st, ctx)
+    return e
+
+
+def histogram(x, lo, hi, nbins, stream=None):
+    """Bin counts of the values of ``x`` (float32 or float64 CUDA tensor):
+    (counts[nbins], below, above, nan)."""
+    import torch
+    lib = load()
+    ctx = context(x.device.index)
+    if x.dtype not in (torch.float32, torch.float64) or not x.is_cuda or not x.is_contiguous():
+        raise ValueError("x must be a contiguous float32/float64 CUDA tensor")
+    c = np.zeros(int(nbins) + 3, dtype=np.int64)
+    st = lib.ad_histogram(ctx, AD_F64 if x.dtype == torch.float64 else AD_F32, x.numel(),
+                          ctypes.c_void_p(x.data_ptr()), float(lo), float(hi), int(nbins),
+                          ctypes.c_void_p(c.ctypes.data), _stream_ptr(stream))
+    _check(st, ctx)
+    return c[:nbins], int(c[nbins]), int(c[nbins + 1]), int(c[nbins + 2])
+
+
+def curl(u, ndim=None, out=None, stream=None):
+    """Vorticity of velocities shaped [..., ndim, *grid]: 2D -> [..., *grid]
+    (dv/dx - du/dy), 3D -> [..., 3, *grid]."""
+    import torch
+    lib = load()
+    ctx = context(u.device.index)
+    if ndim is None:
+        ndim = 3 if u.dim() >= 4 and u.shape[-4] == 3 else 2
+    g, nvel, shape = _velocity_grid(u, ndim, ndim)
+    lead = tuple(u.shape[:u.dim() - ndim - 1])
+    if out is None:
+        oshape = lead + tuple(shape) if ndim == 2 else lead + (3,) + tuple(shape)
+        out = torch.empty(oshape, dtype=u.dtype, device=u.device)
+    st = lib.ad_curl(ctx, ctypes.byref(g), nvel, ctypes.c_void_p(u.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                     _stream_ptr(stream))
+    _check(st, ctx)
+    return out

@@ -61,6 +61,7 @@ struct Plan {
   double gamma = 0.0;
   long long P = 0, SP = 0;
   PassCfg xf, xi, fl, yf, yi;
+  PassCfg sn;                        // preconditioner stencil pass (W rows per block)
   const void* twx = nullptr;
   void *S1 = nullptr, *S2 = nullptr;
   void *R = nullptr, *Pv = nullptr, *Q = nullptr, *Sv = nullptr, *F0 = nullptr;
@@ -133,6 +134,8 @@ struct ad_ctx {
   std::map<std::string, GraphEntry> graphs;
   std::string err;
   int64_t launches = 0;
+  void* stat_buf = nullptr;                   // device scratch of the statistics calls
+  size_t stat_cap = 0;
 };
 
 namespace {
@@ -280,9 +283,15 @@ bool choose_tile(int L, int E, int slots, int div, size_t csize, PassCfg& pc) {
 int pick_E(int L) { return (L % 3 == 0) ? 24 : 16; }
 
 // A method value: one of AD_VANCITTERT .. AD_SD, optionally OR-ed with AD_SPECTRAL.
-bool method_ok(int m) { return m >= 0 && (m & ~(AD_SPECTRAL | 3)) == 0; }
+bool method_ok(int m) {
+  if (m < 0 || (m & ~(AD_SPECTRAL | AD_PRECOND | 3)) != 0) return false;
+  // the preconditioner is defined for CG in physical space
+  if ((m & AD_PRECOND) && ((m & 3) != AD_CG || (m & AD_SPECTRAL))) return false;
+  return true;
+}
 int method_base(int m) { return m & 3; }
 bool method_spectral(int m) { return (m & AD_SPECTRAL) != 0; }
+bool method_precond(int m) { return (m & AD_PRECOND) != 0; }
 
 std::string plan_key(const ad_grid* g, int batch) {
   char buf[256];
@@ -369,11 +378,30 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
     p->yi = p->yf;
   }
   if (!ok) { delete p; return fail(ctx, AD_ERR_ARG, "no tiling for this grid"); }
+  {
+    // stencil tiles: W rows (a power of two dividing Ny, at most 16) with the
+    // staged rows (W + 2 in 2D, 3 W + 2 in 3D) within 64 KB of shared memory
+    const size_t row = (size_t)p->nx * rs;
+    int W = 1;
+    for (int w = 2; w <= 16 && p->ny % w == 0; w *= 2) {
+      const int nr = p->ndim == 3 ? 3 * w + 2 : w + 2;
+      if ((size_t)nr * row > 64 * 1024) break;
+      W = w;
+    }
+    const int nr = p->ndim == 3 ? 3 * W + 2 : W + 2;
+    p->sn = PassCfg{};
+    p->sn.W = W;
+    p->sn.smem = (size_t)nr * row;
+    const long long chunks = (long long)W * p->nx / 4;
+    p->sn.T = (int)std::min<long long>(256, (chunks + 31) / 32 * 32);
+    p->sn.rcp_a = 1.0f / (float)(p->nx / 4);
+    p->sn.grid = dim3((unsigned)(p->ny / W * p->nz), batch);
+  }
   const size_t vb = (size_t)p->P * batch * rs, sb = (size_t)p->SP * batch * cs;
   if ((s = dmalloc(ctx, p, &p->S1, sb)) != AD_OK ||
       (p->ndim == 3 && (s = dmalloc(ctx, p, &p->S2, sb)) != AD_OK)) { free_plan(p); return s; }
   // partials sized for the narrowest tile the autotuner may pick (1/8 of the default width)
-  const unsigned maxblk = 8 * std::max(p->xi.grid.x, p->fl.grid.x) + 8;
+  const unsigned maxblk = 8 * std::max(p->xi.grid.x, p->fl.grid.x) + p->sn.grid.x + 8;
   p->maxblk = maxblk;
   if ((s = dmalloc(ctx, p, (void**)&p->st, sizeof(FieldState) * batch)) != AD_OK ||
       (s = dmalloc(ctx, p, (void**)&p->part, sizeof(double) * 4 * maxblk * batch)) != AD_OK ||
@@ -458,7 +486,8 @@ struct Fwd { int op = XF_COPY; const void* A = nullptr; const void* B = nullptr;
 struct Flt { int op = FI_NONE; int stage = SS_NONE; };
 struct Inv { int op = XI_STORE; const void* A = nullptr; const void* B = nullptr; const void* C = nullptr;
              void* O1 = nullptr; void* O2 = nullptr; int ndots = 0; int stage = SS_NONE; bool set_cond = false; };
-struct Common { FieldState* st = nullptr; SolveConfig cfg{}; cudaGraphConditionalHandle cond = 0; bool in_graph = false; int force = 0; };
+struct Common { FieldState* st = nullptr; SolveConfig cfg{}; cudaGraphConditionalHandle cond = 0; bool in_graph = false; int force = 0;
+                int ncomp = 0, npairs = 0, pair_code = 0; };
 
 template <typename T>
 PassArgs<T> base_args(const Plan* p, const Common& c) {
@@ -470,9 +499,15 @@ PassArgs<T> base_args(const Plan* p, const Common& c) {
   a.kc2 = (T)(kc * kc);
   a.inv_p = 1.0;                      // physical-space dots are plain sums
   a.gscale = (T)(1.0 / (double)p->P);
+  // preconditioner weights (delta/h_d)^2 = (N_d / (2 pi k_c))^2
+  const double tpk = 2.0 * 3.14159265358979323846 * kc;
+  a.cx = (T)((p->nx / tpk) * (p->nx / tpk));
+  a.cy = (T)((p->ny / tpk) * (p->ny / tpk));
+  a.cz = (T)(p->ndim == 3 ? (p->nz / tpk) * (p->nz / tpk) : 0.0);
   a.S1 = p->S1; a.S2 = p->S2;
   a.st = c.st; a.cfg = c.cfg; a.part = p->part; a.ticket = p->ticket;
   a.cond = c.cond; a.batch = p->batch; a.force = c.force;
+  a.ncomp = c.ncomp; a.npairs = c.npairs; a.pair_code = c.pair_code;
   return a;
 }
 
@@ -547,6 +582,7 @@ struct SolveIO {
   int method;           // AD_VANCITTERT .. AD_SD (the AD_SPECTRAL flag goes to `spectral`)
   bool want_true;
   bool spectral = false;
+  bool precond = false;   // AD_CG with the stencil preconditioner (AD_PRECOND)
 };
 
 // ---------------------------------------------------------------------------
@@ -687,10 +723,31 @@ ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, 
   return enqueue_G<T>(ctx, p, s, fw, Flt{}, iv, c, nl);
 }
 
+// z = M r (the preconditioner stencil) with the dot (r, z) -> rho, beta.
+template <typename T>
+ad_status enqueue_sten(ad_ctx* ctx, Plan* p, cudaStream_t s, const void* r, void* z, const Common& c,
+                       bool clear_cond, int* nl) {
+  PassArgs<T> a = base_args<T>(p, c);
+  a.W = p->sn.W; a.rcp_a = p->sn.rcp_a; a.tfft = p->sn.T;
+  a.op = 0; a.A = (const T*)r; a.O1 = (T*)z;
+  a.ndots = 1; a.stage = SS_PCG_RHO; a.set_cond = 0;
+  a.clear_cond = (clear_cond && c.in_graph) ? 1 : 0;
+  CK(issue<T>(ctx, PK_STEN, p->sn, s, a));
+  ++*nl;
+  return AD_OK;
+}
+
 template <typename T>
 ad_status enqueue_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
   if (io.spectral) return enqueue_spec_body<T>(ctx, p, s, io, c, nl);
   ad_status r;
+  if (io.precond) {                // preconditioned CG: z = M r; then Algorithm 3's pass with p = z + beta p
+    if ((r = enqueue_sten<T>(ctx, p, s, p->R, p->Q, c, true, nl)) != AD_OK) return r;
+    Fwd fw; fw.op = XF_CG; fw.A = p->Q; fw.O1 = io.u; fw.O2 = p->Pv;
+    Flt fl; fl.op = FI_XGX; fl.stage = SS_CG_ALPHA;
+    Inv iv; iv.op = XI_CG; iv.O1 = p->R; iv.ndots = 1; iv.stage = SS_PCG_STOP; iv.set_cond = true;
+    return enqueue_G<T>(ctx, p, s, fw, fl, iv, c, nl);
+  }
   switch (io.method) {
     case AD_VANCITTERT: {          // Algorithm 1: u += r; d = G r; r -= d
       Fwd fw; fw.clear_cond = true; fw.op = XF_VC; fw.A = p->R; fw.O1 = io.u;
@@ -819,8 +876,8 @@ ad_status run_solve(ad_ctx* ctx, Plan* p, const SolveIO& io, double tol, int max
   ad_status st;
   if (ctx->use_graph) {
     char buf[256];
-    snprintf(buf, sizeof buf, "|%d|%d|%a|%d|%p|%p|%p|%d", io.method, io.spectral ? 1 : 0, tol, maxit, io.ubar,
-             io.u, io.u0, io.want_true ? 1 : 0);
+    snprintf(buf, sizeof buf, "|%d|%d|%d|%a|%d|%p|%p|%p|%d", io.method, io.spectral ? 1 : 0, io.precond ? 1 : 0,
+             tol, maxit, io.ubar, io.u, io.u0, io.want_true ? 1 : 0);
     char pk[128];
     snprintf(pk, sizeof pk, "%p", (void*)p);
     const std::string gkey = std::string(pk) + buf;
@@ -897,7 +954,8 @@ double time_kind(ad_ctx* ctx, Plan* p, int method, int kind, int reps) {
   Common c;
   c.st = p->st;
   c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method; c.cfg.hist = p->hist; c.cfg.hist_ld = p->hist_cap;
-  SolveIO io{p->F0, p->Uscratch, nullptr, method_base(method), false, method_spectral(method)};
+  SolveIO io{p->F0, p->Uscratch, nullptr, method_base(method), false, method_spectral(method),
+             method_precond(method)};
   int nl = 0;
   const ad_status s = enqueue_body<T>(ctx, p, nullptr, io, c, &nl);
   ctx->record = nullptr;
@@ -1124,7 +1182,8 @@ ad_status capture_group(ad_ctx* ctx, BatchedGroup& gr, cudaStream_t s, cudaGraph
   const size_t bytes = (size_t)p->P * sizeof(T);
   for (size_t k = 0; k < gr.fields.size(); ++k)
     CK(cudaMemcpyAsync((char*)p->Bin + k * bytes, ubar[gr.fields[k]], bytes, cudaMemcpyDeviceToDevice, s));
-  SolveIO io{p->Bin, p->Bout, nullptr, method_base(method), false, method_spectral(method)};
+  SolveIO io{p->Bin, p->Bout, nullptr, method_base(method), false, method_spectral(method),
+             method_precond(method)};
   ad_status st = enqueue_init<T>(ctx, p, s, io, c, &gr.n_init);
   if (st != AD_OK) return st;
   cudaStreamCaptureStatus cs;
@@ -1233,6 +1292,7 @@ void ad_destroy(ad_ctx* c) {
   for (auto e : c->events) cudaEventDestroy(e);
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->cap2) cudaStreamDestroy(c->cap2);
+  if (c->stat_buf) cudaFree(c->stat_buf);
   delete c;
 }
 
@@ -1256,7 +1316,8 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
   c.st = p->st;
   c.cfg.tol = 0.0; c.cfg.maxit = 1; c.cfg.method = method_base(method); c.cfg.hist = p->hist;
   c.cfg.hist_ld = p->hist_cap;
-  SolveIO io{p->F0, p->Uscratch, nullptr, method_base(method), false, method_spectral(method)};
+  SolveIO io{p->F0, p->Uscratch, nullptr, method_base(method), false, method_spectral(method),
+             method_precond(method)};
   int nl = 0;
   s = p->f64 ? enqueue_body<double>(ctx, p, nullptr, io, c, &nl) : enqueue_body<float>(ctx, p, nullptr, io, c, &nl);
   ctx->record = nullptr;
@@ -1616,7 +1677,8 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
   if ((s = ensure_hist(ctx, p, maxit)) != AD_OK) return s;
   if (method_spectral(method) && (s = ensure_spectral(ctx, p)) != AD_OK) return s;
   cudaStream_t st = (cudaStream_t)stream;
-  SolveIO io{ubar, u_out, u0, method_base(method), true_res != nullptr, method_spectral(method)};
+  SolveIO io{ubar, u_out, u0, method_base(method), true_res != nullptr, method_spectral(method),
+             method_precond(method)};
   int loops = 0, n_body = 0;
   s = p->f64 ? run_solve<double>(ctx, p, io, tol, maxit, st, &loops, &n_body)
              : run_solve<float>(ctx, p, io, tol, maxit, st, &loops, &n_body);
@@ -1642,4 +1704,160 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
   return worst;
 }
 
+// ---------------------------------------------------------------------------
+// Closure and statistics of deconvolved fields.
+
+namespace {
+
+ad_status stat_scratch(ad_ctx* ctx, size_t bytes, void** out) {
+  if (bytes > ctx->stat_cap) {
+    if (ctx->stat_buf) cudaFree(ctx->stat_buf);
+    ctx->stat_buf = nullptr;
+    ctx->stat_cap = 0;
+    if (cudaMalloc(&ctx->stat_buf, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(ctx, AD_ERR_NOMEM, "statistics scratch of " + std::to_string(bytes) + " bytes");
+    }
+    ctx->stat_cap = bytes;
+  }
+  *out = ctx->stat_buf;
+  return AD_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
+}
+
+}  // namespace
+
+ad_status ad_closure(ad_ctx* ctx, const ad_grid* grid, int nvel, int ncomp, const void* ubar, const void* ustar,
+                     void* tau, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (ncomp < 1 || ncomp > 3) return fail(ctx, AD_ERR_ARG, "ncomp must be 1, 2 or 3");
+  if (nvel < 0) return fail(ctx, AD_ERR_ARG, "nvel < 0");
+  const int npairs = ncomp * (ncomp + 1) / 2;
+  if ((long long)nvel * npairs > AD_MAX_BATCH) return fail(ctx, AD_ERR_ARG, "nvel * pairs > AD_MAX_BATCH");
+  if (nvel == 0) { ctx->launches = 0; return AD_OK; }
+  if (!ubar || !ustar || !tau) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
+  if (((uintptr_t)ubar | (uintptr_t)ustar | (uintptr_t)tau) & 15)
+    return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  const size_t es = grid->dtype == AD_F64 ? 8 : 4;
+  const long long P = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
+  const size_t nin = (size_t)nvel * ncomp * P * es, nout = (size_t)nvel * npairs * P * es;
+  if (overlaps(tau, nout, ubar, nin) || overlaps(tau, nout, ustar, nin))
+    return fail(ctx, AD_ERR_ARG, "tau must not overlap ubar or ustar");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, nvel * npairs, &p)) != AD_OK) return s;
+  Common c;
+  c.ncomp = ncomp;
+  c.npairs = npairs;
+  int code = 0, q = 0;
+  for (int i = 0; i < ncomp; ++i)
+    for (int j = i; j < ncomp; ++j, ++q) code |= (i | (j << 2)) << (4 * q);
+  c.pair_code = code;
+  Fwd fw; fw.op = XF_MUL; fw.A = ustar;
+  Inv iv; iv.op = XI_TAU; iv.B = ubar; iv.O1 = tau;
+  int nl = 0;
+  cudaStream_t st = (cudaStream_t)stream;
+  s = p->f64 ? enqueue_G<double>(ctx, p, st, fw, Flt{}, iv, c, &nl) : enqueue_G<float>(ctx, p, st, fw, Flt{}, iv, c, &nl);
+  ctx->launches = nl;
+  return s;
+}
+
+ad_status ad_spectrum(ad_ctx* ctx, const ad_grid* grid, int nfields, int ncomp, const void* u, int nbins,
+                      double* E, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (ncomp < 1 || nfields < 0 || nfields % ncomp != 0) return fail(ctx, AD_ERR_ARG, "nfields must be a multiple of ncomp >= 1");
+  if (nbins < 1 || nbins > AD_MAX_SHELLS) return fail(ctx, AD_ERR_ARG, "nbins must be in [1, AD_MAX_SHELLS]");
+  if (nfields > AD_MAX_BATCH) return fail(ctx, AD_ERR_ARG, "nfields > AD_MAX_BATCH");
+  if (nfields == 0) { ctx->launches = 0; return AD_OK; }
+  if (!u || !E) return fail(ctx, AD_ERR_ARG, "NULL pointer");
+  if ((uintptr_t)u & 15) return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, nfields, &p)) != AD_OK) return s;
+  if ((s = ensure_spectral(ctx, p)) != AD_OK) return s;
+  const int ngroups = nfields / ncomp;
+  const size_t bytes = sizeof(double) * (size_t)ngroups * nbins;
+  void* buf = nullptr;
+  if ((s = stat_scratch(ctx, bytes, &buf)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nl = 0;
+  s = p->f64 ? enqueue_fwd_transform<double>(ctx, p, st, u, p->Bh, &nl)
+             : enqueue_fwd_transform<float>(ctx, p, st, u, p->Bh, &nl);
+  if (s != AD_OK) return s;
+  CK(cudaMemsetAsync(buf, 0, bytes, st));
+  const double scale = 1.0 / ((double)p->P * (double)p->P);
+  CK(p->f64 ? launch_shell<double>(p->Bh, p->nx, p->ny, p->nz, p->SP, nfields, ncomp, nbins, scale, (double*)buf, st)
+            : launch_shell<float>(p->Bh, p->nx, p->ny, p->nz, p->SP, nfields, ncomp, nbins, scale, (double*)buf, st));
+  CK(cudaMemcpyAsync(E, buf, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->launches = nl + 1;
+  return AD_OK;
+}
+
+ad_status ad_histogram(ad_ctx* ctx, ad_dtype dtype, int64_t n, const void* x, double lo, double hi, int nbins,
+                       int64_t* counts, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  if (dtype != AD_F32 && dtype != AD_F64) return fail(ctx, AD_ERR_ARG, "dtype must be AD_F32 or AD_F64");
+  if (n < 0 || nbins < 1 || nbins > AD_MAX_HIST_BINS) return fail(ctx, AD_ERR_ARG, "need n >= 0 and 1 <= nbins <= AD_MAX_HIST_BINS");
+  if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi)) return fail(ctx, AD_ERR_ARG, "need finite lo < hi");
+  if (!counts) return fail(ctx, AD_ERR_ARG, "NULL counts");
+  if (n > 0 && !x) return fail(ctx, AD_ERR_ARG, "NULL data");
+  CK(cudaSetDevice(ctx->device));
+  const size_t bytes = sizeof(unsigned long long) * (size_t)(nbins + 3);
+  void* buf = nullptr;
+  ad_status s;
+  if ((s = stat_scratch(ctx, bytes, &buf)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(buf, 0, bytes, st));
+  const double scale = (double)nbins / (hi - lo);
+  if (n > 0) {
+    CK(dtype == AD_F64 ? launch_hist<double>((const double*)x, n, lo, scale, nbins, (unsigned long long*)buf, st)
+                       : launch_hist<float>((const float*)x, n, lo, scale, nbins, (unsigned long long*)buf, st));
+  }
+  std::vector<unsigned long long> h(nbins + 3);
+  CK(cudaMemcpyAsync(h.data(), buf, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int b = 0; b < nbins + 3; ++b) counts[b] = (int64_t)h[b];
+  ctx->launches = n > 0 ? 1 : 0;
+  return AD_OK;
+}
+
+ad_status ad_curl(ad_ctx* ctx, const ad_grid* grid, int nvel, const void* u, void* omega, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  const int ncomp = grid->ndim, nout = grid->ndim == 2 ? 1 : 3;
+  if (nvel < 0 || (long long)nvel * ncomp > AD_MAX_BATCH) return fail(ctx, AD_ERR_ARG, "bad nvel");
+  if (nvel == 0) { ctx->launches = 0; return AD_OK; }
+  if (!u || !omega) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
+  if (((uintptr_t)u | (uintptr_t)omega) & 15) return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  CK(cudaSetDevice(ctx->device));
+  Plan *pin = nullptr, *pout = nullptr;
+  if ((s = get_plan(ctx, grid, nvel * ncomp, &pin)) != AD_OK) return s;
+  if ((s = ensure_spectral(ctx, pin)) != AD_OK) return s;
+  if ((s = get_plan(ctx, grid, nvel * nout, &pout)) != AD_OK) return s;
+  if ((s = ensure_spectral(ctx, pout)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  int nl = 0;
+  s = pin->f64 ? enqueue_fwd_transform<double>(ctx, pin, st, u, pin->Bh, &nl)
+               : enqueue_fwd_transform<float>(ctx, pin, st, u, pin->Bh, &nl);
+  if (s != AD_OK) return s;
+  CK(pin->f64 ? launch_curl<double>(pin->Bh, pout->Uh, pin->nx, pin->ny, pin->nz, pin->SP, nvel, ncomp, st)
+              : launch_curl<float>(pin->Bh, pout->Uh, pin->nx, pin->ny, pin->nz, pin->SP, nvel, ncomp, st));
+  ++nl;
+  s = pout->f64 ? enqueue_inv_transform<double>(ctx, pout, st, pout->Uh, omega, &nl)
+                : enqueue_inv_transform<float>(ctx, pout, st, pout->Uh, omega, &nl);
+  ctx->launches = nl;
+  return s;
+}
+
 }  // extern "C"
+

@@ -32,6 +32,7 @@ enum XfOp : int {
   XF_CG = 2,     // Algorithm 3: U += alpha P; P = R + beta P (first pass: P = R); x = P
   XF_BI_P = 3,   // Algorithm 4: P = R + beta (P - omega Q) (first pass: P = R); x = P
   XF_BI_S = 4,   // Algorithm 4: S = R - alpha Q; x = S
+  XF_MUL = 5,    // closure: x = A_i A_j, field f = pair p of velocity v, A = u* as [v][ncomp][P]
 };
 
 // Epilogue (inverse x pass) opcodes, y = G x.
@@ -44,6 +45,7 @@ enum XiOp : int {
   XI_SD = 5,     // U += alpha R; R -= alpha y; dot (R, R)
   XI_BI_Q = 6,   // Q = y; dot (F0, Q)
   XI_BI_T = 7,   // t = y; U += alpha P + omega S; R = S - omega t; dots (R, R), (F0, R)
+  XI_TAU = 8,    // closure: O1 = B_i B_j - y (B = u_bar as [v][ncomp][P]; pair of field f as in XF_MUL)
 };
 
 // Filter-pass dot opcodes (Parseval sums over the half spectrum).
@@ -86,6 +88,9 @@ struct PassArgs {
   T kc2;                     // k_c^2
   double inv_p;              // scale of the block dots: 1/P for Parseval sums, else 1
   T gscale;                  // 1/P folded into the filter multiply
+  T cx, cy, cz;              // preconditioner stencil weights (delta/h_d)^2 of the x, y, z axes
+  int ncomp, npairs;         // closure: components per velocity, pairs i <= j per velocity
+  int pair_code;             // closure: pair p = (i, j) at bits 4p (i) and 4p + 2 (j)
   void* S1;
   void* S2;
   const T* A;

@@ -86,6 +86,10 @@ __device__ inline void stop_or_continue(FieldState& s, const SolveConfig& cfg, i
 }
 
 __device__ inline void scalar_update(int stage, FieldState& s, const double* d, const SolveConfig& cfg, int f) {
+  if (s.fault) {                 // a bounded wait of this field gave up: its dots are incomplete
+    s.status = -4; s.active = 0; // AD_ERR_TIMEOUT
+    return;
+  }
   switch (stage) {
     case SS_REF:
       s.ref = sqrt(fmax(d[0], 0.0));
@@ -157,6 +161,23 @@ __device__ inline void scalar_update(int stage, FieldState& s, const double* d, 
       }
       break;
     }
+    case SS_PCG_RHO: {           // rho_{n+1} = (r_{n+1}, z_{n+1}); beta_n = rho_{n+1} / rho_n
+      const double rz = d[0];
+      if (!(rz > 0.0) || !finite_d(rz)) {
+        s.status = 2; s.active = 0;                // AD_BREAKDOWN
+        if (s.iter > 0) s.fin_axpy = 1;            // u += alpha p of the last pass is still owed
+      } else if (s.iter == 0) {
+        s.rho = rz;
+      } else {
+        s.beta = rz / s.rho;
+        s.rho = rz;
+      }
+      break;
+    }
+    case SS_PCG_STOP:
+      stop_or_continue(s, cfg, f, d[0]);
+      if (!s.active) s.fin_axpy = 1;
+      break;
     case SS_TRUE:
       s.true_res = s.ref > 0.0 ? sqrt(fmax(d[0], 0.0)) / s.ref : sqrt(fmax(d[0], 0.0));
       break;
@@ -364,6 +385,17 @@ template <typename T> __device__ __forceinline__ V4<T> get_pair(const typename c
   return {{a.x, a.y, b.x, b.y}};
 }
 
+// Component offsets of the closure pair that field f stands for: field f is
+// pair p = f mod npairs of velocity v = f / npairs, whose components i and j
+// start at (v ncomp + i) P and (v ncomp + j) P.
+template <typename T>
+__device__ __forceinline__ void pair_offsets(const PassArgs<T>& a, int f, long long& oi, long long& oj) {
+  const int v = f / a.npairs, p = f - v * a.npairs;
+  const int i = (a.pair_code >> (4 * p)) & 3, j = (a.pair_code >> (4 * p + 2)) & 3;
+  oi = ((long long)v * a.ncomp + i) * a.P;
+  oj = ((long long)v * a.ncomp + j) * a.P;
+}
+
 // x = prologue of the forward x pass for the block's row tile, written into
 // the shared-memory rows as packed complex (z[n] = x[2n] + i x[2n+1]).
 template <typename T, int U>
@@ -438,6 +470,20 @@ __device__ __forceinline__ void xfwd_prologue(const PassArgs<T>& a, typename cpx
         for (int e = 0; e < 4; ++e) so.v[e] = fma(-al, y_[u].v[e], r_[u].v[e]);
         st4(vO3 + g, so);
         put_pair<T>(s + w * ld, q, so);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
+    case XF_MUL: {                                // closure: x = A_i A_j
+      long long oi, oj;
+      pair_offsets(a, (int)blockIdx.y, oi, oj);
+      const long long fb = (long long)blockIdx.y * a.P;
+      auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + (g - fb) + oi); y_[u] = ld4(vA + (g - fb) + oj); };
+      auto fin = [&](int u, int w, int q, long long) {
+        V4<T> xo;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) xo.v[e] = r_[u].v[e] * y_[u].v[e];
+        put_pair<T>(s + w * ld, q, xo);
       };
       stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
       break;
@@ -557,6 +603,21 @@ __device__ __forceinline__ void xinv_epilogue(const PassArgs<T>& a, const typena
       stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
       break;
     }
+    case XI_TAU: {                                // closure: O1 = B_i B_j - y
+      long long oi, oj;
+      pair_offsets(a, (int)blockIdx.y, oi, oj);
+      const long long fb = (long long)blockIdx.y * a.P;
+      auto ldf = [&](int u, long long g) { b_[u] = ld4(vB + (g - fb) + oi); c_[u] = ld4(vB + (g - fb) + oj); };
+      auto fin = [&](int u, int w, int q, long long g) {
+        const V4<T> y = get_pair<T>(s + w * ld, q);
+        V4<T> t;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) t.v[e] = fma(b_[u].v[e], c_[u].v[e], -y.v[e]);
+        st4(vO1 + g, t);
+      };
+      stream_tile<U>(W, nx, rq, base, tid, nthr, ldf, fin);
+      break;
+    }
     default:
       break;
   }
@@ -588,7 +649,15 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
     // only the first of the streaming rounds waits on DRAM
     const long long tb = (long long)a.W * nx * sizeof(T);
     const int op = a.op;
-    prefetch_l2(a.A + base, tb, tid, nthr);
+    if (op == XF_MUL) {
+      long long oi, oj;
+      pair_offsets(a, f, oi, oj);
+      const long long ro = (long long)row0 * nx;
+      prefetch_l2(a.A + oi + ro, tb, tid, nthr);
+      prefetch_l2(a.A + oj + ro, tb, tid, nthr);
+    } else {
+      prefetch_l2(a.A + base, tb, tid, nthr);
+    }
     if (op == XF_VC || (op == XF_CG && !first)) prefetch_l2(a.O1 + base, tb, tid, nthr);
     if ((op == XF_CG || op == XF_BI_P) && !first) prefetch_l2(a.O2 + base, tb, tid, nthr);
     if ((op == XF_BI_P && !first) || op == XF_BI_S) prefetch_l2(a.B + base, tb, tid, nthr);
@@ -648,6 +717,13 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
       if (op == XI_INIT || op == XI_RES || op == XI_BI_Q || op == XI_BI_T) prefetch_l2(a.A + base, tb, tid, nthr);
       if (op == XI_VC || op == XI_CG || op == XI_SD || op == XI_BI_T) prefetch_l2(a.O1 + base, tb, tid, nthr);
       if (op == XI_SD) prefetch_l2(a.O2 + base, tb, tid, nthr);
+      if (op == XI_TAU) {
+        long long oi, oj;
+        pair_offsets(a, f, oi, oj);
+        const long long ro = (long long)row0 * nx;
+        prefetch_l2(a.B + oi + ro, tb, tid, nthr);
+        prefetch_l2(a.B + oj + ro, tb, tid, nthr);
+      }
       if (op == XI_BI_T) {
         prefetch_l2(a.B + base, tb, tid, nthr);
         prefetch_l2(a.C + base, tb, tid, nthr);

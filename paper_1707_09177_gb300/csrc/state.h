@@ -21,7 +21,8 @@ struct FieldState {
   int early;         // BiCGSTAB: this pass ends with omega = 0 (s small)
   int fin_axpy;      // CG: the final u += alpha p is still owed
   int have_ref;      // ref supplied by a separate pass (explicit u0)
-  int pad[2];
+  int fault;         // a bounded device wait of this field gave up (AD_ERR_TIMEOUT)
+  int pad;
 };
 
 struct SolveConfig {
@@ -45,6 +46,8 @@ enum ScalarStage : int {
   SS_BI_END = 8,     // dots: (r,r), (f0, r)                 -> stop test, beta
   SS_TRUE = 9,       // dots: (res,res)                      -> true residual
   SS_SD_ALPHA = 10,  // dots: (r, G r)                       -> alpha_n (Algorithm 2)
+  SS_PCG_RHO = 11,   // dots: (r, z), z = M r                -> rho, beta (preconditioned CG)
+  SS_PCG_STOP = 12,  // dots: (r, r)                         -> stop test (preconditioned CG)
 };
 
 }  // namespace gad

@@ -71,6 +71,22 @@ def test_single_mode_hand_value():
     np.testing.assert_allclose(oracle.apply_preconditioner(f, 0.25), expect * f, rtol=1e-13, atol=1e-13)
 
 
+@pytest.mark.parametrize("shape,gamma", [((32, 48), 0.01), ((16, 8, 12), 0.1)])
+def test_float32_evaluation_within_rounding_bound(shape, gamma):
+    """The float32 evaluation differs from the float64 one of the same float32
+    input by rounding only: per term at most a few float32 ulps of the
+    magnitudes that enter it."""
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal(shape).astype(np.float32).astype(np.float64)
+    z64 = oracle.apply_preconditioner(x, gamma)
+    z32 = oracle.apply_preconditioner_f32(x, gamma)
+    cs = oracle.stencil_coefficients(shape, gamma)
+    scale = np.abs(x) + sum(c * (2 * np.abs(x) + np.abs(np.roll(x, 1, a)) + np.abs(np.roll(x, -1, a)))
+                            for a, c in enumerate(cs))
+    assert np.all(np.abs(z32 - z64) <= 8 * 2.0 ** -24 * scale)
+    assert np.max(np.abs(z32 - z64) / scale) > 0           # genuinely float32
+
+
 def test_second_order_consistency_with_the_exact_inverse():
     """For a fixed smooth mode, M_hat(k) -> 1 + |k|^2/k_c^2 (the symbol of
     G^{-1}) with an error that falls by 4x when the grid is refined 2x at a
