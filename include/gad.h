@@ -308,6 +308,15 @@ ad_status ad_histogram(ad_ctx* ctx, ad_dtype dtype, int64_t n, const void* x, do
  * Device pointers; omega must not overlap u. Enqueued on `stream`. */
 ad_status ad_curl(ad_ctx* ctx, const ad_grid* grid, int nvel, const void* u, void* omega, void* stream);
 
+/* Time limit of the bounded device waits (the preconditioner's wait for its
+ * staged rows; default 1e9 ns). A block whose wait runs out takes no part in
+ * the result, waits up to 1 s more for its own copies, and its field ends
+ * with AD_ERR_TIMEOUT; the context stays usable. ns = 0 makes each such wait
+ * a single non-blocking test, which in practice always runs out: that is how
+ * the timeout path is tested without a fault. Cached solve graphs are
+ * dropped. No counterpart in the paper. */
+ad_status ad_set_wait_limit(ad_ctx* ctx, uint64_t ns);
+
 /* Enables (1, default) or disables (0) capture of each solve into one CUDA
  * graph whose iteration loop is a device-side conditional while node. With 0
  * the host launches the iteration body in chunks and polls the device

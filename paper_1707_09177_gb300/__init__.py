@@ -45,7 +45,7 @@ AD_F32, AD_F64 = 0, 1
 EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvolve_batched", "ad_time_pass",
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
             "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
-            "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl")
+            "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl", "ad_set_wait_limit")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec", 8: "sten"}
 
 
@@ -123,6 +123,8 @@ def load(path=None):
     lib.ad_histogram.restype = c_i
     lib.ad_curl.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_p, c_p, c_p]
     lib.ad_curl.restype = c_i
+    lib.ad_set_wait_limit.argtypes = [c_p, ctypes.c_uint64]
+    lib.ad_set_wait_limit.restype = c_i
     _lib = lib
     return lib
 
@@ -143,6 +145,13 @@ def context(device=None):
 
 def set_graph_mode(enable, device=None):
     load().ad_set_graph_mode(context(device), 1 if enable else 0)
+
+
+def set_wait_limit(ns, device=None):
+    """Time limit (ns) of the library's bounded device waits; 0 makes each a
+    single test (used to exercise the timeout path)."""
+    ctx = context(device)
+    _check(load().ad_set_wait_limit(ctx, int(ns)), ctx)
 
 
 def last_launch_count(device=None):

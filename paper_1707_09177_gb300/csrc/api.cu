@@ -136,6 +136,7 @@ struct ad_ctx {
   int64_t launches = 0;
   void* stat_buf = nullptr;                   // device scratch of the statistics calls
   size_t stat_cap = 0;
+  unsigned long long wait_ns = 1000000000ull; // limit of bounded device waits
 };
 
 namespace {
@@ -487,7 +488,7 @@ struct Flt { int op = FI_NONE; int stage = SS_NONE; };
 struct Inv { int op = XI_STORE; const void* A = nullptr; const void* B = nullptr; const void* C = nullptr;
              void* O1 = nullptr; void* O2 = nullptr; int ndots = 0; int stage = SS_NONE; bool set_cond = false; };
 struct Common { FieldState* st = nullptr; SolveConfig cfg{}; cudaGraphConditionalHandle cond = 0; bool in_graph = false; int force = 0;
-                int ncomp = 0, npairs = 0, pair_code = 0; };
+                int ncomp = 0, npairs = 0, pair_code = 0; unsigned long long wait_ns = 1000000000ull; };
 
 template <typename T>
 PassArgs<T> base_args(const Plan* p, const Common& c) {
@@ -508,6 +509,7 @@ PassArgs<T> base_args(const Plan* p, const Common& c) {
   a.st = c.st; a.cfg = c.cfg; a.part = p->part; a.ticket = p->ticket;
   a.cond = c.cond; a.batch = p->batch; a.force = c.force;
   a.ncomp = c.ncomp; a.npairs = c.npairs; a.pair_code = c.pair_code;
+  a.wait_ns = c.wait_ns;
   return a;
 }
 
@@ -868,6 +870,7 @@ ad_status run_solve(ad_ctx* ctx, Plan* p, const SolveIO& io, double tol, int max
                     int* loops_out, int* n_body_out) {
   Common c;
   c.st = p->st;
+  c.wait_ns = ctx->wait_ns;
   c.cfg.tol = tol;
   c.cfg.maxit = maxit;
   c.cfg.method = io.method;
@@ -1172,6 +1175,7 @@ ad_status capture_group(ad_ctx* ctx, BatchedGroup& gr, cudaStream_t s, cudaGraph
   Plan* p = gr.p;
   Common c;
   c.st = p->st;
+  c.wait_ns = ctx->wait_ns;
   c.cfg.tol = tol;
   c.cfg.maxit = maxit;
   c.cfg.method = method_base(method);
@@ -1730,6 +1734,16 @@ bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
 }
 
 }  // namespace
+
+ad_status ad_set_wait_limit(ad_ctx* ctx, uint64_t ns) {
+  if (!ctx) return AD_ERR_ARG;
+  if (ns == ctx->wait_ns) return AD_OK;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaDeviceSynchronize());
+  drop_graphs(ctx);               // cached graphs hold the old limit
+  ctx->wait_ns = ns;
+  return AD_OK;
+}
 
 ad_status ad_closure(ad_ctx* ctx, const ad_grid* grid, int nvel, int ncomp, const void* ubar, const void* ustar,
                      void* tau, void* stream) {

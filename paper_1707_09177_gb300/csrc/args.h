@@ -91,6 +91,7 @@ struct PassArgs {
   T cx, cy, cz;              // preconditioner stencil weights (delta/h_d)^2 of the x, y, z axes
   int ncomp, npairs;         // closure: components per velocity, pairs i <= j per velocity
   int pair_code;             // closure: pair p = (i, j) at bits 4p (i) and 4p + 2 (j)
+  unsigned long long wait_ns;  // limit of a bounded device wait (0: test once)
   void* S1;
   void* S2;
   const T* A;

@@ -44,20 +44,21 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Waits for phase `parity` of the mbarrier; false after `limit_ns` of waiting.
+// Waits for phase `parity` of the mbarrier; false after `limit_ns` of waiting
+// (limit_ns = 0: one non-blocking test).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   const uint64_t t0 = global_ns();
   for (;;) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > limit_ns) return false;
+    if (limit_ns == 0 || global_ns() - t0 > limit_ns) return false;
   }
 }
 
@@ -120,11 +121,14 @@ __global__ void __launch_bounds__(256) k_sten(PassArgs<T> a) {
             ::"r"(dst), "l"(src), "r"(row_bytes), "r"(b) : "memory");
       }
     }
-    ok = mbar_wait_bounded(b, 0u, 1000000000ull);
+    // every thread waits; the block gives up as a whole if any thread did
+    ok = __syncthreads_and(mbar_wait_bounded(b, 0u, a.wait_ns) ? 1 : 0) != 0;
     if (!ok) {
-      // flag the field and wait (bounded again) for this block's copies
+      // flag the field and wait (bounded, 1 s) for this block's copies to land
+      // before its shared memory is released
       if (tid == 0 && st) atomicExch(&st->fault, 1);
       mbar_wait_bounded(b, 0u, 1000000000ull);
+      __syncthreads();
     }
   }
   if (act && ok) {

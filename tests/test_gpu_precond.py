@@ -219,3 +219,23 @@ def test_bench_workload_full_size(gad):
     base, runs = ensemble_runs("pcg", ub[9].astype(np.float64), 0.01, 0.0, 3, "f32")
     tolf, spread = field_tolerance(base, runs, "f32")
     assert _rel(res.u[9].double().cpu().numpy(), base.u) < tolf, spread
+
+
+def test_bounded_wait_times_out_cleanly(gad):
+    """The stencil's wait for its staged rows is bounded. With the limit at 0
+    (one non-blocking test, which cannot see copies just issued) every block
+    gives up: the solve reports AD_ERR_TIMEOUT for each field instead of
+    hanging, and the context then solves normally again."""
+    _, ub = _problem((64, 96), 3, 0.1)
+    t = _to_gpu(np.stack([ub, ub]))
+    ok = gad.deconvolve(t, 0.1, method="pcg", tol=1e-6, maxit=100, ndim=2)
+    gad.set_wait_limit(0)
+    try:
+        with pytest.raises(gad.GadError) as e:
+            gad.deconvolve(t, 0.1, method="pcg", tol=1e-6, maxit=100, ndim=2)
+        assert e.value.status == gad.AD_ERR_TIMEOUT
+    finally:
+        gad.set_wait_limit(1_000_000_000)
+    again = gad.deconvolve(t, 0.1, method="pcg", tol=1e-6, maxit=100, ndim=2)
+    assert list(again.status) == [gad.AD_OK, gad.AD_OK]
+    np.testing.assert_array_equal(again.u.cpu().numpy(), ok.u.cpu().numpy())
