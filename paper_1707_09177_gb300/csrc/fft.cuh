@@ -141,6 +141,31 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void dft(C* v)
 // exact small-integer quotient for q < 2^20: floor((x + 0.5) * rcp)
 __device__ __forceinline__ int fquot(int x, float rcp) { return __float2int_rz((float(x) + 0.5f) * rcp); }
 
+// Shared-memory row accessors for the inner stages.
+template <typename C>
+struct SmemRows {
+  C* s;
+  int ld;
+  __device__ __forceinline__ C operator()(int w, int i) const { return s[w * ld + phys(i)]; }
+  __device__ __forceinline__ void operator()(int w, int i, const C& x) const { s[w * ld + phys(i)] = x; }
+};
+
+template <class X> struct is_rows { static constexpr bool value = false; };
+template <class C> struct is_rows<SmemRows<C>> { static constexpr bool value = true; };
+
+// A run of R elements i0 + r*st (r < R) of one shared-memory row has a
+// constant padded stride when st is a multiple of 16 (phys stride st + st/16)
+// or when st = 1 and the run stays inside one 16-element block (R divides 16
+// and i0 is a multiple of R): then phys(i0 + r*st) = phys(i0) + r*pst and the
+// stage addresses its R elements with one add each instead of recomputing
+// phys() per element. Returns pst, or 0 when the stride is not constant.
+template <int R>
+__device__ __forceinline__ int run_stride(int st) {
+  if ((st & 15) == 0) return st + (st >> 4);
+  if (st == 1 && (16 % R) == 0) return 1;
+  return 0;
+}
+
 // One radix-R Stockham stage over the whole tile. Every thread owns E/R
 // butterflies; all inputs are held in registers before any output is
 // written, so a stage may overwrite its own input.
@@ -161,6 +186,7 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
   int wrow[NB], jj[NB];
   const bool on = tid < nthr;     // threads beyond the FFT's thread count only join barriers
   if (on) {
+    const int lst = is_rows<Load>::value ? run_stride<R>(lr) : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int bi = tid + b * nthr;
@@ -168,25 +194,43 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
       const int j = bi - w * lr;
       wrow[b] = w;
       jj[b] = j;
+      if constexpr (is_rows<Load>::value) {
+        if (lst) {
+          const C* p = load.s + w * load.ld + phys(j);
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[b][r] = p[r * lst];
+          continue;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = load(w, j + r * lr);
     }
   }
   if (mid_barrier) __syncthreads();
   if (on) {
+    const int est = is_rows<Emit>::value ? run_stride<R>(sg.ns) : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = jj[b];
       const int k = j - sg.ns * fquot(j, sg.rcp_ns);
       if (sg.ns > 1) {
+        const int kt = k * sg.tw_step;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C w = tw[r * k * sg.tw_step];
+          const C w = tw[r * kt];
           v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
         }
       }
       dft<R, INV>(v[b]);
       const int o = (j - k) * R + k;
+      if constexpr (is_rows<Emit>::value) {
+        if (est) {
+          C* p = emit.s + wrow[b] * emit.ld + phys(o);
+#pragma unroll
+          for (int r = 0; r < R; ++r) p[r * est] = v[b][r];
+          continue;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) emit(wrow[b], o + r * sg.ns, v[b][r]);
     }
@@ -210,6 +254,7 @@ __device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C*
   int wrow[NB], jj[NB];
   const bool on = tid < nthr;
   if (on) {
+    const int lst = is_rows<Load>::value ? run_stride<R>(lr) : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int bi = tid + b * nthr;
@@ -217,37 +262,46 @@ __device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C*
       const int j = bi - w * lr;
       wrow[b] = w;
       jj[b] = j;
+      if constexpr (is_rows<Load>::value) {
+        if (lst) {
+          const C* p = load.s + w * load.ld + phys(j);
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[b][r] = p[r * lst];
+          continue;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) v[b][r] = load(w, j + r * lr);
     }
   }
   if (mid_barrier) __syncthreads();
   if (on) {
+    const int est = is_rows<Emit>::value ? run_stride<R>(1) : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = jj[b];                  // k = j: ns = L/R exceeds every j
       if (sg.ns > 1) {
+        const int kt = j * sg.tw_step;
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[r * j * sg.tw_step]);
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[r * kt]);
       }
       dft<R, false>(v[b]);
 #pragma unroll
       for (int r = 0; r < R; ++r) mul(wrow[b], j + r * lr, v[b][r]);
       dft<R, true>(v[b]);
+      if constexpr (is_rows<Emit>::value) {
+        if (est) {
+          C* p = emit.s + wrow[b] * emit.ld + phys(j * R);
+#pragma unroll
+          for (int r = 0; r < R; ++r) p[r] = v[b][r];
+          continue;
+        }
+      }
 #pragma unroll
       for (int r = 0; r < R; ++r) emit(wrow[b], j * R + r, v[b][r]);
     }
   }
 }
-
-// Shared-memory row accessors for the inner stages.
-template <typename C>
-struct SmemRows {
-  C* s;
-  int ld;
-  __device__ __forceinline__ C operator()(int w, int i) const { return s[w * ld + phys(i)]; }
-  __device__ __forceinline__ void operator()(int w, int i, const C& x) const { s[w * ld + phys(i)] = x; }
-};
 
 // Stage q of a plan that lives in kernel-parameter space. Constant indices
 // only: a runtime index into a parameter array would force a local-memory

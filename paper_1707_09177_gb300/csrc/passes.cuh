@@ -322,13 +322,13 @@ template <typename T> __device__ __forceinline__ void st2(T* p, T a, T b) {
   *reinterpret_cast<C*>(p) = C{a, b};
 }
 
-// Float32, E = 16: the x and y passes run at 64 registers (4 blocks of 256
-// per SM) and the filter pass, which keeps two FFT stages' worth of state
-// live, at 80 (3 blocks); a few spilled words cost less than the latency the
-// extra warps hide (measured: the filter pass 21-26% faster than at 2 blocks
-// and 128 registers, the x/y passes 5-17% faster than at 3 blocks).
+// Float32, E = 16: every pass runs at 64 registers (4 blocks of 256 per SM),
+// the filter pass too although it keeps two FFT stages' worth of state live;
+// a few spilled words cost less than the latency the extra warps hide
+// (measured: the filter pass 28-31% faster than at 2 blocks and 128
+// registers, the x/y passes 5-17% faster than at 3 blocks and 80).
 #define GAD_BOUNDS(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 4 : 2)
-#define GAD_BOUNDS_FILT(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 3 : 2)
+#define GAD_BOUNDS_FILT(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 4 : 2)
 
 // ---------------------------------------------------------------------------
 // Row-tile streaming for the fused Krylov prologue/epilogue of the x passes.
