@@ -62,7 +62,7 @@ def _peaks():
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("fft.cuh", "passes.cuh", "spectral.cuh", "args.h"):
+    for f in ("fft.cuh", "passes.cuh", "spectral.cuh"):
         with open(os.path.join(ROOT, "paper_1707_09177_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -129,6 +129,29 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def rank_seeds(rank, batch):
+    """Seeds of the fields rank `rank` solves: weak scaling, each rank its own
+    `batch` fields, disjoint across ranks."""
+    return list(range(rank * batch, rank * batch + batch))
+
+
+def max_over_ranks(x, device):
+    """The maximum of a per-rank float over all ranks (the job is as slow as
+    its slowest rank); x itself when not distributed."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mpoints(world, batch, points, seconds):
+    """Mpoints/s of the whole job: every rank's fields over the max time."""
+    return world * batch * points / seconds / 1e6
 
 
 def _pass_bytes(kind, op, P, SP, B, method):
@@ -226,6 +249,8 @@ def _extra_workloads(gad, dev, extras):
         rs, ts = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3,
                                                space="spectral"))
         rp, tp = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3))
+        rq, tq = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3,
+                                               space="spectral"))
         out["velocity3d_256_f32"] = {"mpoints_s": 3 * n ** 3 / t / 1e6, "ms": t * 1e3, "iterations": its,
                                      "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches,
                                      "spectral": {"mpoints_s": 3 * n ** 3 / ts / 1e6, "ms": ts * 1e3,
@@ -233,7 +258,10 @@ def _extra_workloads(gad, dev, extras):
                                                   "converged": bool(np.all(rs.status == gad.AD_OK))},
                                      "pcg": {"mpoints_s": 3 * n ** 3 / tp / 1e6, "ms": tp * 1e3,
                                              "iterations": [int(x) for x in rp.iterations],
-                                             "converged": bool(np.all(rp.status == gad.AD_OK))}}
+                                             "converged": bool(np.all(rp.status == gad.AD_OK))},
+                                     "pcg_spectral": {"mpoints_s": 3 * n ** 3 / tq / 1e6, "ms": tq * 1e3,
+                                                      "iterations": [int(x) for x in rq.iterations],
+                                                      "converged": bool(np.all(rq.status == gad.AD_OK))}}
         if "closure" in extras:
             out["closure_256"] = _closure_stats(gad, ub, r.u, n)
         del ub, r, rp
@@ -354,6 +382,9 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
     gad.deconvolve(ub, gamma, method="pcg", tol=1e-6, maxit=2, ndim=3, history=False)
     pcg, t_pcg = timed(lambda: gad.deconvolve(ub, gamma, method="pcg", tol=1e-6, maxit=4000, ndim=3,
                                               history=False))
+    gad.deconvolve(ub, gamma, method="pcg", tol=1e-6, maxit=2, ndim=3, history=False, space="spectral")
+    pcs, t_pcs = timed(lambda: gad.deconvolve(ub, gamma, method="pcg", tol=1e-6, maxit=4000, ndim=3,
+                                              history=False, space="spectral"))
     diff = float(torch.linalg.vector_norm(learned.u - plain.u) / torch.linalg.vector_norm(plain.u))
     pts = 3.0 * n ** 3
     t_learned = t_inf + t_solve
@@ -377,7 +408,10 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
         "wall_time_ratio_plain_over_learned": t_plain / t_learned,
         "preconditioned_cg": {"ms": t_pcg * 1e3, "mpoints_s": pts / t_pcg / 1e6,
                               "iterations": [int(x) for x in pcg.iterations],
-                              "converged": bool(np.all(pcg.status == gad.AD_OK))},
+                              "converged": bool(np.all(pcg.status == gad.AD_OK)),
+                              "spectral": {"ms": t_pcs * 1e3, "mpoints_s": pts / t_pcs / 1e6,
+                                           "iterations": [int(x) for x in pcs.iterations],
+                                           "converged": bool(np.all(pcs.status == gad.AD_OK))}},
         "rel_l2_learned_vs_plain_solution": diff,
         "train": {"pairs": npairs, "shape": [n_train] * 3, "epochs": epochs, "batch": batch, "lr": lr,
                   "seconds": t_train, "loss_per_epoch": [float(x) for x in hist],
@@ -454,7 +488,7 @@ def main():
     B, gamma, tol = args.batch, WORKLOAD["gamma"], WORKLOAD["tol"]
     n = WORKLOAD["shape"]
     P = n[0] * n[1]
-    seeds = list(range(rank * B, rank * B + B))
+    seeds = rank_seeds(rank, B)
     gad.load()
     if args.host_loop:
         gad.set_graph_mode(False)
@@ -490,12 +524,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
     clocks = clk.summary()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * B * P / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
+    value = whole_job_mpoints(ws, B, P, ms * 1e-3)
     iters = [int(x) for x in res.iterations]
     ok = bool(np.all(res.status == gad.AD_OK))
 
@@ -518,13 +548,9 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     barrier()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, dev)
     nbytes = ubar.numel() * ubar.element_size()
-    e2e = {"value": ws * B * P / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": nbytes,
+    e2e = {"value": whole_job_mpoints(ws, B, P, e2e_s), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -544,7 +570,7 @@ def main():
         # comparison methods on the same batch (one timed solve each)
         methods = {}
         for m, mi, sp in (("cg", 3000, "physical"), ("bicgstab", 3000, "physical"), ("pcg", 3000, "physical"),
-                          ("vancittert", VC_MAXIT, "physical"), ("cg", 3000, "spectral"),
+                          ("vancittert", VC_MAXIT, "physical"), ("cg", 3000, "spectral"), ("pcg", 3000, "spectral"),
                           ("bicgstab", 3000, "spectral"), ("vancittert", VC_MAXIT, "spectral")):
             step(m, maxit=mi, space=sp)
             torch.cuda.synchronize()

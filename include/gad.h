@@ -67,8 +67,8 @@ typedef enum {
    * arithmetic; in floating point the result differs by rounding. Accepted
    * by ad_deconvolve, ad_deconvolve_batched, ad_time_pass and ad_autotune. */
   AD_SPECTRAL = 4,
-  /* Flag OR-ed into AD_CG (physical space only; any other combination is
-   * AD_ERR_ARG): preconditioned CG. The paper solves Eq. tau3 without a
+  /* Flag OR-ed into AD_CG, in physical space or with AD_SPECTRAL (with any
+   * other method it is AD_ERR_ARG): preconditioned CG. The paper solves Eq. tau3 without a
    * preconditioner; this flag adds the textbook preconditioned CG with M,
    * the second-order periodic finite-difference version of the filter's
    * differential inverse G^{-1} = I - delta^2 Laplacian (Section 4, Eq. df):
@@ -79,7 +79,9 @@ typedef enum {
    * symmetric positive definite and commutes with G; M G has its spectrum in
    * [4/pi^2, 1], so the pass count no longer grows with |k|^2/k_c^2. Per
    * pass: one stencil pass (z = M r, (r, z)) and one application of G with
-   * Algorithm 3's updates (p = z + beta p). Same stopping rules and history
+   * Algorithm 3's updates (p = z + beta p); in spectral space M is the
+   * pointwise multiply by its symbol M_hat(k) = 1 + sum_d 4 c_d sin^2(pi k_d /
+   * N_d) inside two streaming passes. Same stopping rules and history
    * (unpreconditioned residual ||r_n|| / ||u_bar - G u_bar||); rho_n =
    * (r_n, z_n) <= 0 or not finite is AD_BREAKDOWN. Accepted by
    * ad_deconvolve, ad_deconvolve_batched and ad_time_pass. */
@@ -310,11 +312,11 @@ ad_status ad_curl(ad_ctx* ctx, const ad_grid* grid, int nvel, const void* u, voi
 
 /* Time limit of the bounded device waits (the preconditioner's wait for its
  * staged rows; default 1e9 ns). A block whose wait runs out takes no part in
- * the result, waits up to 1 s more for its own copies, and its field ends
- * with AD_ERR_TIMEOUT; the context stays usable. ns = 0 makes each such wait
- * a single non-blocking test, which in practice always runs out: that is how
- * the timeout path is tested without a fault. Cached solve graphs are
- * dropped. No counterpart in the paper. */
+ * the result, waits up to 1 s more for its own copies still in flight, and
+ * its field ends with AD_ERR_TIMEOUT; the context stays usable. ns = 0 makes
+ * every such wait give up at once: that is how the timeout path is tested
+ * without a fault. Cached solve graphs are dropped. No counterpart in the
+ * paper. */
 ad_status ad_set_wait_limit(ad_ctx* ctx, uint64_t ns);
 
 /* Enables (1, default) or disables (0) capture of each solve into one CUDA

@@ -39,7 +39,7 @@ import math
 
 import numpy as np
 
-from .solvers import (STATUS_BREAKDOWN, STATUS_MAXIT, STATUS_OK, _Arith, _finish, _h, _Physical, _pre_loop,
+from .solvers import (STATUS_BREAKDOWN, STATUS_MAXIT, STATUS_OK, _Arith, _finish, _h, _pre_loop, _space,
                       _start)
 from .spectral import cutoff_wavenumber
 
@@ -87,14 +87,22 @@ def preconditioner_symbol(shape, gamma):
     return out
 
 
-def preconditioned_cg(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, precond=True):
+def preconditioned_cg(ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, precond=True,
+                      space="physical"):
     """The preconditioned CG iteration of the module docstring. precond=False
-    uses M = I (Algorithm 3 itself)."""
+    uses M = I (Algorithm 3 itself). space="spectral" runs the same steps on
+    the half spectra (solvers.py's spectral space): M is circulant, so it
+    becomes the pointwise multiply by M_hat, and the iterates equal the
+    physical-space ones in exact arithmetic."""
     ar = _Arith(precision)
-    sp = _Physical(np.shape(ubar), gamma)
+    shape = np.shape(ubar)
+    sp = _space(space, shape, gamma)
     ubar, ref, u, r = _start(ubar, gamma, u0, ar, sp)
     if not precond:
-        M = lambda x: np.asarray(x, dtype=np.float64)          # noqa: E731
+        M = lambda x: np.asarray(x)                            # noqa: E731
+    elif space == "spectral":
+        mh = preconditioner_symbol(shape, gamma)[..., : shape[-1] // 2 + 1]
+        M = lambda x: mh * x                                   # noqa: E731
     elif ar.f32:
         M = lambda x: apply_preconditioner_f32(x, gamma)       # noqa: E731
     else:

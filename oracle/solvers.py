@@ -369,11 +369,10 @@ _METHODS = {
 
 def solve(method, ubar, gamma, tol=0.0, maxit=5, u0=None, precision="f64", record=False, space="physical"):
     """Dispatch by method name: 'vancittert', 'sd', 'cg', 'bicgstab', or 'pcg'
-    (preconditioned CG, precond.py; physical space only)."""
+    (preconditioned CG, precond.py)."""
     if method == "pcg":
-        if space != "physical":
-            raise ValueError("pcg runs in physical space only")
         from .precond import preconditioned_cg
-        return preconditioned_cg(ubar, gamma, tol=tol, maxit=maxit, u0=u0, precision=precision, record=record)
+        return preconditioned_cg(ubar, gamma, tol=tol, maxit=maxit, u0=u0, precision=precision, record=record,
+                                 space=space)
     return _METHODS[method](ubar, gamma, tol=tol, maxit=maxit, u0=u0,
                             precision=precision, record=record, space=space)

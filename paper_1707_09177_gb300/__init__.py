@@ -148,8 +148,8 @@ def set_graph_mode(enable, device=None):
 
 
 def set_wait_limit(ns, device=None):
-    """Time limit (ns) of the library's bounded device waits; 0 makes each a
-    single test (used to exercise the timeout path)."""
+    """Time limit (ns) of the library's bounded device waits; 0 makes each give
+    up at once (used to exercise the timeout path)."""
     ctx = context(device)
     _check(load().ad_set_wait_limit(ctx, int(ns)), ctx)
 

@@ -48,6 +48,7 @@ int pow2_part(long long n) {
 
 struct PassCfg {
   int E = 0, W = 0, T = 0, ld = 0;
+  int chunk = 0;                     // stencil pass: march positions per block
   size_t smem = 0;
   FftPlan fft{};
   FftPlan fft_inv{};
@@ -286,8 +287,8 @@ int pick_E(int L) { return (L % 3 == 0) ? 24 : 16; }
 // A method value: one of AD_VANCITTERT .. AD_SD, optionally OR-ed with AD_SPECTRAL.
 bool method_ok(int m) {
   if (m < 0 || (m & ~(AD_SPECTRAL | AD_PRECOND | 3)) != 0) return false;
-  // the preconditioner is defined for CG in physical space
-  if ((m & AD_PRECOND) && ((m & 3) != AD_CG || (m & AD_SPECTRAL))) return false;
+  // the preconditioner is defined for CG (in either space)
+  if ((m & AD_PRECOND) && (m & 3) != AD_CG) return false;
   return true;
 }
 int method_base(int m) { return m & 3; }
@@ -380,23 +381,35 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
   }
   if (!ok) { delete p; return fail(ctx, AD_ERR_ARG, "no tiling for this grid"); }
   {
-    // stencil tiles: W rows (a power of two dividing Ny, at most 16) with the
-    // staged rows (W + 2 in 2D, 3 W + 2 in 3D) within 64 KB of shared memory
+    // stencil pass: the march runs along z (3D) or y (2D); a ring of four
+    // slices in shared memory, a slice being W + 2 rows in 3D (W a power of
+    // two dividing Ny, at most 16, four slices within 96 KB) and one row in
+    // 2D; the march axis is cut into chunks (a divisor of its length) until
+    // the launch has 4 blocks per SM or the chunks are down to 4 positions
     const size_t row = (size_t)p->nx * rs;
     int W = 1;
-    for (int w = 2; w <= 16 && p->ny % w == 0; w *= 2) {
-      const int nr = p->ndim == 3 ? 3 * w + 2 : w + 2;
-      if ((size_t)nr * row > 64 * 1024) break;
-      W = w;
+    if (p->ndim == 3)
+      for (int w = 2; w <= 16 && p->ny % w == 0; w *= 2) {
+        if (4 * (size_t)(w + 2) * row > 96 * 1024) break;
+        W = w;
+      }
+    const int srows = p->ndim == 3 ? W + 2 : 1;
+    const int nmarch = p->ndim == 3 ? p->nz : p->ny;
+    const long long tiles = p->ndim == 3 ? p->ny / W : 1;
+    int chunk = nmarch;
+    for (int nch = 1; nch <= nmarch; ++nch) {
+      if (nmarch % nch != 0) continue;
+      chunk = nmarch / nch;
+      if (tiles * nch * batch >= 4 * 152 || chunk <= 4) break;
     }
-    const int nr = p->ndim == 3 ? 3 * W + 2 : W + 2;
     p->sn = PassCfg{};
     p->sn.W = W;
-    p->sn.smem = (size_t)nr * row;
-    const long long chunks = (long long)W * p->nx / 4;
-    p->sn.T = (int)std::min<long long>(256, (chunks + 31) / 32 * 32);
+    p->sn.chunk = chunk;
+    p->sn.smem = 4 * (size_t)srows * row;
+    const long long vec4 = (long long)W * p->nx / 4;
+    p->sn.T = (int)std::min<long long>(256, (vec4 + 31) / 32 * 32);
     p->sn.rcp_a = 1.0f / (float)(p->nx / 4);
-    p->sn.grid = dim3((unsigned)(p->ny / W * p->nz), batch);
+    p->sn.grid = dim3((unsigned)(tiles * (nmarch / chunk)), batch);
   }
   const size_t vb = (size_t)p->P * batch * rs, sb = (size_t)p->SP * batch * cs;
   if ((s = dmalloc(ctx, p, &p->S1, sb)) != AD_OK ||
@@ -665,7 +678,8 @@ ad_status enqueue_spec_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO&
     Spec ref; ref.op = SP_REF; ref.stage = SS_REF; ref.A = p->Bh;
     if ((r = enqueue_spec<T>(ctx, p, s, ref, c, nl)) != AD_OK) return r;
   }
-  Spec in; in.op = SP_INIT; in.stage = SS_INIT; in.A = p->Bh;
+  Spec in; in.op = io.precond ? SP_PCG_INIT : SP_INIT; in.stage = io.precond ? SS_PCG_INIT : SS_INIT;
+  in.ndots = io.precond ? 2 : 1; in.A = p->Bh;
   in.B = io.u0 ? p->Uh : nullptr;
   in.O1 = io.u0 ? nullptr : p->Uh;
   in.O2 = p->Rh;
@@ -688,6 +702,13 @@ ad_status enqueue_spec_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO&
       return enqueue_spec<T>(ctx, p, s, k2, c, nl);
     }
     case AD_CG: {
+      if (io.precond) {            // preconditioned CG: z = M_hat r, p = z + beta p; u += alpha p, r -= alpha G p
+        Spec k1; k1.op = SP_PCG_P; k1.stage = SS_CG_ALPHA; k1.A = p->Rh; k1.O1 = p->Ph; k1.clear_cond = true;
+        if ((r = enqueue_spec<T>(ctx, p, s, k1, c, nl)) != AD_OK) return r;
+        Spec k2; k2.op = SP_PCG; k2.stage = SS_PCG_END; k2.ndots = 2; k2.A = p->Ph; k2.O1 = p->Uh; k2.O2 = p->Rh;
+        k2.set_cond = true;
+        return enqueue_spec<T>(ctx, p, s, k2, c, nl);
+      }
       Spec k1; k1.op = SP_CG_P; k1.stage = SS_CG_ALPHA; k1.A = p->Rh; k1.O1 = p->Ph; k1.clear_cond = true;
       if ((r = enqueue_spec<T>(ctx, p, s, k1, c, nl)) != AD_OK) return r;
       Spec k2; k2.op = SP_CG; k2.stage = SS_CG_BETA; k2.A = p->Ph; k2.O1 = p->Uh; k2.O2 = p->Rh; k2.set_cond = true;
@@ -730,7 +751,7 @@ template <typename T>
 ad_status enqueue_sten(ad_ctx* ctx, Plan* p, cudaStream_t s, const void* r, void* z, const Common& c,
                        bool clear_cond, int* nl) {
   PassArgs<T> a = base_args<T>(p, c);
-  a.W = p->sn.W; a.rcp_a = p->sn.rcp_a; a.tfft = p->sn.T;
+  a.W = p->sn.W; a.chunk = p->sn.chunk; a.rcp_a = p->sn.rcp_a; a.tfft = p->sn.T;
   a.op = 0; a.A = (const T*)r; a.O1 = (T*)z;
   a.ndots = 1; a.stage = SS_PCG_RHO; a.set_cond = 0;
   a.clear_cond = (clear_cond && c.in_graph) ? 1 : 0;

@@ -70,6 +70,9 @@ enum SpOp : int {
   SP_BI_S = 8,    // Algorithm 4: s = A - alpha G B, t = G s; d = (s, s), (s, t), (t, t)
   SP_BI_END = 9,  // Algorithm 4: s, t from O2 and A; O1 += alpha A + omega s; O2 = s - omega t;
                   //              d = (O2, O2), (B, O2)
+  SP_PCG_INIT = 10, // as SP_INIT, and d[1] = (r, M r) (preconditioned CG: rho_0)
+  SP_PCG_P = 11,  // preconditioned CG: O1 = M A (first pass) or M A + beta O1; d = (O1, G O1)
+  SP_PCG = 12,    // preconditioned CG: O1 += alpha A; O2 -= alpha G A; d = (O2, O2), (O2, M O2)
 };
 
 template <typename T>
@@ -91,7 +94,8 @@ struct PassArgs {
   T cx, cy, cz;              // preconditioner stencil weights (delta/h_d)^2 of the x, y, z axes
   int ncomp, npairs;         // closure: components per velocity, pairs i <= j per velocity
   int pair_code;             // closure: pair p = (i, j) at bits 4p (i) and 4p + 2 (j)
-  unsigned long long wait_ns;  // limit of a bounded device wait (0: test once)
+  unsigned long long wait_ns;  // limit of a bounded device wait (0: give up at once)
+  int chunk;                 // preconditioner stencil: positions of the march axis per block
   void* S1;
   void* S2;
   const T* A;

@@ -95,7 +95,8 @@ __device__ inline void scalar_update(int stage, FieldState& s, const double* d, 
       s.ref = sqrt(fmax(d[0], 0.0));
       s.have_ref = 1;
       break;
-    case SS_INIT: {
+    case SS_INIT:
+    case SS_PCG_INIT: {
       const double rr = d[0];
       if (!s.have_ref) s.ref = sqrt(fmax(rr, 0.0));
       s.iter = 0;
@@ -112,6 +113,10 @@ __device__ inline void scalar_update(int stage, FieldState& s, const double* d, 
       else if (h0 <= cfg.tol) { s.status = 0; s.active = 0; }
       else if (cfg.maxit <= 0) { s.status = 1; s.active = 0; }
       else { s.status = 0; s.active = 1; }
+      if (stage == SS_PCG_INIT && s.active) {
+        s.rho = d[1];                             // rho_0 = (r_0, z_0)
+        if (!(d[1] > 0.0) || !finite_d(d[1])) { s.status = 2; s.active = 0; }
+      }
       break;
     }
     case SS_VC:                  // Algorithms 1 and 2: end of a pass
@@ -178,6 +183,15 @@ __device__ inline void scalar_update(int stage, FieldState& s, const double* d, 
       stop_or_continue(s, cfg, f, d[0]);
       if (!s.active) s.fin_axpy = 1;
       break;
+    case SS_PCG_END: {           // stop test on (r, r); then rho_{n+1} = (r, z), beta_n
+      stop_or_continue(s, cfg, f, d[0]);
+      if (s.active) {
+        const double rz = d[1];
+        if (!(rz > 0.0) || !finite_d(rz)) { s.status = 2; s.active = 0; }
+        else { s.beta = rz / s.rho; s.rho = rz; }
+      }
+      break;
+    }
     case SS_TRUE:
       s.true_res = s.ref > 0.0 ? sqrt(fmax(d[0], 0.0)) / s.ref : sqrt(fmax(d[0], 0.0));
       break;
@@ -264,7 +278,7 @@ __device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, boo
     const unsigned prevg = atomicAdd(a.ticket, 1u);
     if (prevg == gridDim.y - 1u) {                        // every field is reduced
       __threadfence();
-      if (a.stage == SS_INIT) a.ticket[1] = 0u;
+      if (a.stage == SS_INIT || a.stage == SS_PCG_INIT) a.ticket[1] = 0u;
       if (a.set_cond) {
         unsigned any = 0;
         for (int g = 0; g < a.batch; ++g) any |= (*(volatile const int*)&a.st[g].active != 0);
@@ -713,25 +727,6 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
   Acc<T> acc[3];
   if (act) {
     const long long base = (long long)f * a.P + (long long)row0 * nx;
-    {
-      // the epilogue's input vectors, fetched into L2 while the FFT runs
-      const long long tb = (long long)a.W * nx * sizeof(T);
-      const int op = a.op;
-      if (op == XI_INIT || op == XI_RES || op == XI_BI_Q || op == XI_BI_T) prefetch_l2(a.A + base, tb, tid, nthr);
-      if (op == XI_VC || op == XI_CG || op == XI_SD || op == XI_BI_T) prefetch_l2(a.O1 + base, tb, tid, nthr);
-      if (op == XI_SD) prefetch_l2(a.O2 + base, tb, tid, nthr);
-      if (op == XI_TAU) {
-        long long oi, oj;
-        pair_offsets(a, f, oi, oj);
-        const long long ro = (long long)row0 * nx;
-        prefetch_l2(a.B + oi + ro, tb, tid, nthr);
-        prefetch_l2(a.B + oj + ro, tb, tid, nthr);
-      }
-      if (op == XI_BI_T) {
-        prefetch_l2(a.B + base, tb, tid, nthr);
-        prefetch_l2(a.C + base, tb, tid, nthr);
-      }
-    }
     const C* S1 = reinterpret_cast<const C*>(a.S1) + (long long)f * a.SP + (long long)z * a.kxn * a.ny + y0;
     load_transposed<C, 8>(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
     __syncthreads();
@@ -756,6 +751,29 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
     __syncthreads();
     SmemRows<C> rows{s, a.ld};
     fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
+    {
+      // the epilogue's input vectors, fetched into L2 as whole tiles just
+      // before the epilogue streams them: only its first round waits on DRAM.
+      // (Fetched at block start instead, they stayed in L2 through the FFT and
+      // were partly evicted before use: 1.29x the algorithmic DRAM traffic
+      // for four input vectors, measured.)
+      const long long tb = (long long)a.W * nx * sizeof(T);
+      const int op = a.op;
+      if (op == XI_INIT || op == XI_RES || op == XI_BI_Q || op == XI_BI_T) prefetch_l2(a.A + base, tb, tid, nthr);
+      if (op == XI_VC || op == XI_CG || op == XI_SD || op == XI_BI_T) prefetch_l2(a.O1 + base, tb, tid, nthr);
+      if (op == XI_SD) prefetch_l2(a.O2 + base, tb, tid, nthr);
+      if (op == XI_TAU) {
+        long long oi, oj;
+        pair_offsets(a, f, oi, oj);
+        const long long ro = (long long)row0 * nx;
+        prefetch_l2(a.B + oi + ro, tb, tid, nthr);
+        prefetch_l2(a.B + oj + ro, tb, tid, nthr);
+      }
+      if (op == XI_BI_T) {
+        prefetch_l2(a.B + base, tb, tid, nthr);
+        prefetch_l2(a.C + base, tb, tid, nthr);
+      }
+    }
     const T al = st ? T(st->alpha) : T(0), om = st ? T(st->omega) : T(0);
     Acc<T> acc0, acc1;
     xinv_epilogue<T, 2>(a, s, base, al, om, acc0, acc1, tid, nthr);

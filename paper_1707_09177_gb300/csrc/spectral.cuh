@@ -72,6 +72,9 @@ __global__ void GAD_BOUNDS(T, E) k_linv(PassArgs<T> a) {
 __device__ __forceinline__ float ghat(float kc2, float k2) { return __fdividef(kc2, kc2 + k2); }
 __device__ __forceinline__ double ghat(double kc2, double k2) { return kc2 / (kc2 + k2); }
 
+__device__ __forceinline__ float sinpi_t(float x) { return sinpif(x); }
+__device__ __forceinline__ double sinpi_t(double x) { return sinpi(x); }
+
 // Inputs of one element pair (two complex values = four reals) of a spectral pass.
 template <typename T>
 struct SpIn {
@@ -83,7 +86,9 @@ __device__ __forceinline__ void sp_load(SpIn<T>& x, const T* __restrict__ vA, co
                                         const T* vO1, const T* vO2, long long o, bool first) {
   switch (OP) {
     case SP_REF: x.a = ld4(vA + o); break;
-    case SP_INIT: x.a = ld4(vA + o); if (vB) x.b = ld4(vB + o); break;
+    case SP_INIT: case SP_PCG_INIT: x.a = ld4(vA + o); if (vB) x.b = ld4(vB + o); break;
+    case SP_PCG_P: x.a = ld4(vA + o); if (!first) x.o1 = ld4(vO1 + o); break;
+    case SP_PCG: x.a = ld4(vA + o); x.o1 = ld4(vO1 + o); x.o2 = ld4(vO2 + o); break;
     case SP_VC: case SP_SD: x.o1 = ld4(vO1 + o); x.o2 = ld4(vO2 + o); break;
     case SP_SD_A: x.a = ld4(vA + o); break;
     case SP_CG_P: x.a = ld4(vA + o); if (!first) x.o1 = ld4(vO1 + o); break;
@@ -98,7 +103,7 @@ __device__ __forceinline__ void sp_load(SpIn<T>& x, const T* __restrict__ vA, co
 // Updates of one element pair and its dot terms; d[k] receives the pair's
 // sum of the k-th inner product (four FMA-formed products, weight applied).
 template <typename T, int OP>
-__device__ __forceinline__ void sp_compute(SpIn<T>& x, const T* g, T wgt, T al, T be, T om, bool first,
+__device__ __forceinline__ void sp_compute(SpIn<T>& x, const T* g, const T* mh, T wgt, T al, T be, T om, bool first,
                                            bool has_b, T* d) {
   d[0] = d[1] = d[2] = T(0);
 #pragma unroll
@@ -114,6 +119,29 @@ __device__ __forceinline__ void sp_compute(SpIn<T>& x, const T* g, T wgt, T al, 
         const T r = fma(-g[e], xv, x.a.v[e]);
         x.o2.v[e] = r;
         d[0] = fma(r, r, d[0]);
+        break;
+      }
+      case SP_PCG_INIT: {
+        const T xv = has_b ? x.b.v[e] : x.a.v[e];
+        const T r = fma(-g[e], xv, x.a.v[e]);
+        x.o2.v[e] = r;
+        d[0] = fma(r, r, d[0]);
+        d[1] = fma(r, mh[e] * r, d[1]);
+        break;
+      }
+      case SP_PCG_P: {                            // z = M r; p = z (first) or z + beta p
+        const T z = mh[e] * x.a.v[e];
+        const T p = first ? z : fma(be, x.o1.v[e], z);
+        x.o1.v[e] = p;
+        d[0] = fma(p, g[e] * p, d[0]);
+        break;
+      }
+      case SP_PCG: {                              // u += alpha p; r -= alpha G p
+        x.o1.v[e] = fma(al, x.a.v[e], x.o1.v[e]);
+        const T r = fma(-al, g[e] * x.a.v[e], x.o2.v[e]);
+        x.o2.v[e] = r;
+        d[0] = fma(r, r, d[0]);
+        d[1] = fma(r, mh[e] * r, d[1]);
         break;
       }
       case SP_VC: {
@@ -178,13 +206,13 @@ __device__ __forceinline__ void sp_compute(SpIn<T>& x, const T* g, T wgt, T al, 
 template <typename T, int OP>
 __device__ __forceinline__ void sp_store(const SpIn<T>& x, const T* vB, T* vO1, T* vO2, T* vO3, long long o) {
   switch (OP) {
-    case SP_INIT:
+    case SP_INIT: case SP_PCG_INIT:
       if (vO1) st4(vO1 + o, x.a);
       st4(vO2 + o, x.o2);
       if (vO3) st4(vO3 + o, x.o2);
       break;
-    case SP_VC: case SP_SD: case SP_CG: case SP_BI_END: st4(vO1 + o, x.o1); st4(vO2 + o, x.o2); break;
-    case SP_CG_P: case SP_BI_P: st4(vO1 + o, x.o1); break;
+    case SP_VC: case SP_SD: case SP_CG: case SP_BI_END: case SP_PCG: st4(vO1 + o, x.o1); st4(vO2 + o, x.o2); break;
+    case SP_CG_P: case SP_BI_P: case SP_PCG_P: st4(vO1 + o, x.o1); break;
     default: break;
   }
 }
@@ -232,6 +260,15 @@ __global__ void __launch_bounds__(256) k_spec(PassArgs<T> a) {
         g[0] = g[1] = ghat(kc2, T(k2r + ka * ka));
         g[2] = g[3] = ghat(kc2, T(k2r + kb * kb));
       };
+      // preconditioned CG: M_hat(k) = 1 + sum_d 4 c_d sin^2(pi k_d / N_d), the
+      // symbol of the periodic finite-difference inverse of G
+      constexpr bool pcg = OP == SP_PCG_INIT || OP == SP_PCG_P || OP == SP_PCG;
+      const T cl = three_d ? a.cz : a.cy;
+      auto mpair = [&](int c, T mrow, T* m) {
+        const T sa = sinpi_t(T(2 * c) / T(L)), sb = sinpi_t(T(2 * c + 1) / T(L));
+        m[0] = m[1] = T(1) + mrow + T(4) * cl * sa * sa;
+        m[2] = m[3] = T(1) + mrow + T(4) * cl * sb * sb;
+      };
       for (long long row = r0 + ro; row < r1; row += K) {
         int kx, k2r;
         if (three_d) {
@@ -244,6 +281,15 @@ __global__ void __launch_bounds__(256) k_spec(PassArgs<T> a) {
           k2r = kx * kx;
         }
         const T wgt = (kx == 0 || kx == nxh) ? T(1) : T(2);
+        T mrow = T(0);
+        if constexpr (pcg) {
+          const T sx = sinpi_t(T(kx) / T(a.nx));
+          mrow = T(4) * a.cx * sx * sx;
+          if (three_d) {
+            const T sy = sinpi_t(T(row - (long long)kx * ny) / T(ny));
+            mrow += T(4) * a.cy * sy * sy;
+          }
+        }
         const long long rb = fo + row * L * 2;
         int c = c0;
         for (; c + cstep < H; c += 2 * cstep) {           // two element pairs per step
@@ -251,11 +297,15 @@ __global__ void __launch_bounds__(256) k_spec(PassArgs<T> a) {
           const long long o0 = rb + 4LL * c, o1 = rb + 4LL * (c + cstep);
           sp_load<T, OP>(x0, vA, vB, vO1, vO2, o0, first);
           sp_load<T, OP>(x1, vA, vB, vO1, vO2, o1, first);
-          T g0[4], g1[4], d0[3], d1[3];
+          T g0[4], g1[4], m0[4], m1[4], d0[3], d1[3];
           gpair(c, k2r, g0);
           gpair(c + cstep, k2r, g1);
-          sp_compute<T, OP>(x0, g0, wgt, al, be, om, first, has_b, d0);
-          sp_compute<T, OP>(x1, g1, wgt, al, be, om, first, has_b, d1);
+          if constexpr (pcg) {
+            mpair(c, mrow, m0);
+            mpair(c + cstep, mrow, m1);
+          }
+          sp_compute<T, OP>(x0, g0, m0, wgt, al, be, om, first, has_b, d0);
+          sp_compute<T, OP>(x1, g1, m1, wgt, al, be, om, first, has_b, d1);
           sp_store<T, OP>(x0, vB, vO1, vO2, vO3, o0);
           sp_store<T, OP>(x1, vB, vO1, vO2, vO3, o1);
 #pragma unroll
@@ -268,9 +318,10 @@ __global__ void __launch_bounds__(256) k_spec(PassArgs<T> a) {
           SpIn<T> x0;
           const long long o0 = rb + 4LL * c;
           sp_load<T, OP>(x0, vA, vB, vO1, vO2, o0, first);
-          T g0[4], d0[3];
+          T g0[4], m0[4], d0[3];
           gpair(c, k2r, g0);
-          sp_compute<T, OP>(x0, g0, wgt, al, be, om, first, has_b, d0);
+          if constexpr (pcg) mpair(c, mrow, m0);
+          sp_compute<T, OP>(x0, g0, m0, wgt, al, be, om, first, has_b, d0);
           sp_store<T, OP>(x0, vB, vO1, vO2, vO3, o0);
 #pragma unroll
           for (int k = 0; k < 3; ++k) acc[k].add(d0[k]);
@@ -294,6 +345,9 @@ cudaError_t launch_spec(dim3 grid, cudaStream_t s, const PassArgs<T>& a) {
     case SP_BI_P: k_spec<T, SP_BI_P><<<grid, 256, 0, s>>>(a); break;
     case SP_BI_S: k_spec<T, SP_BI_S><<<grid, 256, 0, s>>>(a); break;
     case SP_BI_END: k_spec<T, SP_BI_END><<<grid, 256, 0, s>>>(a); break;
+    case SP_PCG_INIT: k_spec<T, SP_PCG_INIT><<<grid, 256, 0, s>>>(a); break;
+    case SP_PCG_P: k_spec<T, SP_PCG_P><<<grid, 256, 0, s>>>(a); break;
+    case SP_PCG: k_spec<T, SP_PCG><<<grid, 256, 0, s>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

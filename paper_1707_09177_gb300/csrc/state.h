@@ -48,6 +48,8 @@ enum ScalarStage : int {
   SS_SD_ALPHA = 10,  // dots: (r, G r)                       -> alpha_n (Algorithm 2)
   SS_PCG_RHO = 11,   // dots: (r, z), z = M r                -> rho, beta (preconditioned CG)
   SS_PCG_STOP = 12,  // dots: (r, r)                         -> stop test (preconditioned CG)
+  SS_PCG_INIT = 13,  // dots: (r0, r0), (r0, z0)             -> h_0, start; rho = (r0, z0)
+  SS_PCG_END = 14,   // dots: (r, r), (r, z)                 -> stop test, then rho, beta
 };
 
 }  // namespace gad

@@ -9,14 +9,12 @@
 // M G to [4/pi^2, 1]. The paper has no preconditioner; this is the textbook
 // preconditioned CG with that M.
 //
-// One block owns a tile of W consecutive rows (y0 .. y0+W-1) of one z plane.
-// Its halo -- rows y0-1 and y0+W of the plane (periodic in y) and, in 3D, the
-// tile's rows in planes z-1 and z+1 (periodic in z) -- and the tile itself
-// are staged in shared memory by bulk asynchronous copies (one per row, the
-// rows are contiguous runs of nx values) that signal an mbarrier; the x
-// neighbours wrap inside each staged row. The wait on the mbarrier is bounded
-// in time: a block that gives up flags its field (AD_ERR_TIMEOUT) and takes
-// no part in the result.
+// Rows are staged in shared memory by bulk asynchronous copies (one per row:
+// the rows are contiguous runs of nx values) that complete on mbarriers; the
+// x neighbours wrap inside each staged row. Every wait on an mbarrier is
+// bounded in time: a block that gives up flags its field (AD_ERR_TIMEOUT),
+// waits (bounded) for its copies still in flight and takes no part in the
+// result.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -45,8 +43,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // Waits for phase `parity` of the mbarrier; false after `limit_ns` of waiting
-// (limit_ns = 0: one non-blocking test).
+// (limit_ns = 0: gives up at once, which is how the timeout path is tested).
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
+  if (limit_ns == 0) return false;
   const uint64_t t0 = global_ns();
   for (;;) {
     uint32_t done;
@@ -58,114 +57,154 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (limit_ns == 0 || global_ns() - t0 > limit_ns) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 
-// z = M r over the block's row tile, with the inner product (r, z).
-//   A = r, O1 = z; W = rows per tile; cx, cy, cz = c_d of the x, y, z axes.
-// Grid: x = (ny / W) * nz tiles, y = fields. Shared memory: (W + 2) rows in
-// 2D, (3 W + 2) rows in 3D, nx values each.
+// z = M r with the inner product (r, z), marching along the outermost axis
+// (z in 3D, y in 2D). A block owns `chunk` consecutive positions m0 ..
+// m0+chunk-1 of that axis and, in 3D, a tile of W rows y0 .. y0+W-1. The rows
+// one position needs -- a "slice": in 3D the tile's rows of plane m with its
+// periodic y-halo rows (W + 2 rows), in 2D row m itself -- are staged by bulk
+// copies (one per row, completing on the slot's mbarrier) into a ring of four
+// slots. Output m reads slices m-1, m, m+1; slices m+2 and m+3 are in flight
+// meanwhile, so every row is read from memory once per block (plus the two
+// boundary slices of the chunk and, in 3D, the y halo).
+//   A = r, O1 = z; W = tile rows (3D), chunk = positions per block;
+//   grid: x = (ny / W) * (nz / chunk) in 3D, ny / chunk in 2D; y = fields;
+//   shared memory: 4 slices.
 template <typename T>
 __global__ void __launch_bounds__(256) k_sten(PassArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t bar;
-  T* rows = reinterpret_cast<T*>(smem_raw);
+  __shared__ __align__(8) uint64_t bars[4];
+  T* ring = reinterpret_cast<T*>(smem_raw);
   const int f = blockIdx.y;
   if (a.clear_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
-  const int tid = threadIdx.x, nthr = blockDim.x;
-  const int nx = a.nx, ny = a.ny, nz = a.nz, W = a.W;
+  const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31;
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
   const bool three_d = nz > 1;
-  const int tiles_y = ny / W;
-  const int zp = blockIdx.x / tiles_y;
-  const int y0 = (blockIdx.x - zp * tiles_y) * W;
-  const int nrows = three_d ? 3 * W + 2 : W + 2;
+  const int W = three_d ? a.W : 1;
+  const int srows = three_d ? W + 2 : 1;
+  const int nmarch = three_d ? nz : ny;
+  const int chunk = a.chunk;
+  const int tiles_y = three_d ? ny / W : 1;
+  const int ct = blockIdx.x / tiles_y;
+  const int y0 = (blockIdx.x - ct * tiles_y) * W;
+  const int m0 = ct * chunk;
   const long long fbase = (long long)f * a.P;
+  const long long slice_elems = (long long)srows * nx;
+  const uint32_t row_bytes = (uint32_t)(nx * sizeof(T));
+  const uint32_t slice_bytes = row_bytes * (uint32_t)srows;
   Acc<T> acc[3];
-  bool ok = true;
+  auto slot = [&](int s) { return (s - (m0 - 1)) & 3; };
+  // warp 0: stage slice s (march position, periodic) into its slot
+  auto issue = [&](int s) {
+    const int q = slot(s);
+    int mm = s % nmarch;
+    if (mm < 0) mm += nmarch;
+    const uint32_t b = smem_u32(&bars[q]);
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(slice_bytes) : "memory");
+    __syncwarp();
+    for (int r = lane; r < srows; r += 32) {
+      long long row;
+      if (three_d) {
+        int yy = y0 - 1 + r;
+        yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+        row = (long long)mm * ny + yy;
+      } else {
+        row = mm;
+      }
+      const T* src = a.A + fbase + row * nx;
+      const uint32_t dst = smem_u32(ring + (long long)q * slice_elems + (long long)r * nx);
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                   ::"r"(dst), "l"(src), "r"(row_bytes), "r"(b) : "memory");
+    }
+  };
   if (act) {
-    const uint32_t b = smem_u32(&bar);
-    const uint32_t row_bytes = (uint32_t)(nx * sizeof(T));
     if (tid == 0) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+      for (int q = 0; q < 4; ++q) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[q])) : "memory");
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid < 32) {
-      if (tid == 0) {
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                     ::"r"(b), "r"(row_bytes * (uint32_t)nrows) : "memory");
-      }
-      __syncwarp();
-      // row slot s: 0 .. W+1 -> plane zp, rows y0-1 .. y0+W;
-      //             W+2+i    -> plane zp-1, row y0+i;  2W+2+i -> plane zp+1, row y0+i
-      for (int s = tid; s < nrows; s += 32) {
-        int zz = zp, yy;
-        if (s < W + 2) {
-          yy = y0 - 1 + s;
-          yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
-        } else if (s < 2 * W + 2) {
-          zz = zp == 0 ? nz - 1 : zp - 1;
-          yy = y0 + (s - (W + 2));
-        } else {
-          zz = zp == nz - 1 ? 0 : zp + 1;
-          yy = y0 + (s - (2 * W + 2));
-        }
-        const T* src = a.A + fbase + ((long long)zz * ny + yy) * nx;
-        const uint32_t dst = smem_u32(rows + (long long)s * nx);
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-            ::"r"(dst), "l"(src), "r"(row_bytes), "r"(b) : "memory");
-      }
-    }
-    // every thread waits; the block gives up as a whole if any thread did
-    ok = __syncthreads_and(mbar_wait_bounded(b, 0u, a.wait_ns) ? 1 : 0) != 0;
-    if (!ok) {
-      // flag the field and wait (bounded, 1 s) for this block's copies to land
-      // before its shared memory is released
-      if (tid == 0 && st) atomicExch(&st->fault, 1);
-      mbar_wait_bounded(b, 0u, 1000000000ull);
-      __syncthreads();
-    }
-  }
-  if (act && ok) {
+    const int last = m0 + chunk;                     // the last slice a block needs
+    const int pre = min(m0 + 2, last);
+    if (tid < 32)
+      for (int s = m0 - 1; s <= pre; ++s) issue(s);
+    unsigned ph = 0u, pending = 0u;                  // per slot: parity to wait for, issued and not waited
+    for (int s = m0 - 1; s <= pre; ++s) pending |= 1u << slot(s);
+    // waits for slice s; false (block-uniform) when the bounded wait gave up
+    auto wait = [&](int s) -> bool {
+      const int q = slot(s);
+      const bool got = __syncthreads_and(mbar_wait_bounded(smem_u32(&bars[q]), (ph >> q) & 1u, a.wait_ns) ? 1 : 0) != 0;
+      if (got) { ph ^= 1u << q; pending &= ~(1u << q); }
+      return got;
+    };
+    bool ok = wait(m0 - 1) && wait(m0);
     const T cx = a.cx, cy = a.cy, cz = a.cz;
     const int qn = nx >> 2;
     T* __restrict__ out = a.O1;
     Acc<T> rz;
-    for (int c = tid; c < W * qn; c += nthr) {
-      const int w = fquot(c, a.rcp_a);
-      const int x0 = 4 * (c - w * qn);
-      const T* rc = rows + (long long)(w + 1) * nx;
-      const V4<T> cv = ld4(rc + x0), nv = ld4(rc - nx + x0), sv = ld4(rc + nx + x0);
-      const T xl = rc[x0 == 0 ? nx - 1 : x0 - 1];
-      const T xr = rc[x0 + 4 == nx ? 0 : x0 + 4];
-      V4<T> bv{}, tv{};
-      if (three_d) {
-        bv = ld4(rows + (long long)(W + 2 + w) * nx + x0);
-        tv = ld4(rows + (long long)(2 * W + 2 + w) * nx + x0);
-      }
-      V4<T> zo;
+    for (int m = m0; ok && m < last; ++m) {
+      if (!wait(m + 1)) { ok = false; break; }
+      const T* sp = ring + (long long)slot(m - 1) * slice_elems;
+      const T* sc = ring + (long long)slot(m) * slice_elems;
+      const T* sn = ring + (long long)slot(m + 1) * slice_elems;
+      const int mm = m >= nmarch ? m - nmarch : m;
+      for (int c = tid; c < W * qn; c += nthr) {
+        const int w = three_d ? fquot(c, a.rcp_a) : 0;
+        const int x0 = 4 * (c - w * qn);
+        // 3D: centre row w+1 of slice m, y neighbours rows w and w+2 of slice m,
+        //     z neighbours row w+1 of slices m-1 and m+1
+        // 2D: centre slice m, y neighbours slices m-1 and m+1
+        const T* rc = sc + (long long)(three_d ? w + 1 : 0) * nx;
+        const T* rn = three_d ? rc - nx : sp;
+        const T* rs = three_d ? rc + nx : sn;
+        const V4<T> cv = ld4(rc + x0), nv = ld4(rn + x0), sv = ld4(rs + x0);
+        const T xl = rc[x0 == 0 ? nx - 1 : x0 - 1];
+        const T xr = rc[x0 + 4 == nx ? 0 : x0 + 4];
+        V4<T> bv{}, tv{};
+        if (three_d) {
+          bv = ld4(sp + (long long)(w + 1) * nx + x0);
+          tv = ld4(sn + (long long)(w + 1) * nx + x0);
+        }
+        V4<T> zo;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        // every operation rounded separately, in this order (no contraction):
-        // z = ((r + c_x d_x) + c_y d_y) + c_z d_z, d = (2 r - left) - right
-        const T r = cv.v[e];
-        const T two = r + r;
-        const T dx = sub_rn(sub_rn(two, e == 0 ? xl : cv.v[e - 1]), e == 3 ? xr : cv.v[e + 1]);
-        const T dy = sub_rn(sub_rn(two, nv.v[e]), sv.v[e]);
-        T z = add_rn(r, mul_rn(cx, dx));
-        z = add_rn(z, mul_rn(cy, dy));
-        if (three_d) z = add_rn(z, mul_rn(cz, sub_rn(sub_rn(two, bv.v[e]), tv.v[e])));
-        zo.v[e] = z;
-        rz.add_prod(r, z);
+        for (int e = 0; e < 4; ++e) {
+          // every operation rounded separately, in this order (no contraction):
+          // z = ((r + c_x d_x) + c_y d_y) + c_z d_z, d = (2 r - left) - right
+          const T r = cv.v[e];
+          const T two = r + r;
+          const T dx = sub_rn(sub_rn(two, e == 0 ? xl : cv.v[e - 1]), e == 3 ? xr : cv.v[e + 1]);
+          const T dy = sub_rn(sub_rn(two, nv.v[e]), sv.v[e]);
+          T z = add_rn(r, mul_rn(cx, dx));
+          z = add_rn(z, mul_rn(cy, dy));
+          if (three_d) z = add_rn(z, mul_rn(cz, sub_rn(sub_rn(two, bv.v[e]), tv.v[e])));
+          zo.v[e] = z;
+          rz.add_prod(r, z);
+        }
+        const long long orow = three_d ? (long long)mm * ny + y0 + w : (long long)mm;
+        st4(out + fbase + orow * nx + x0, zo);
       }
-      st4(out + fbase + ((long long)zp * ny + y0 + w) * nx + x0, zo);
+      __syncthreads();                               // slice m-1 is free
+      if (m + 3 <= last) {
+        if (tid < 32) issue(m + 3);
+        pending |= 1u << slot(m + 3);
+      }
     }
-    acc[0] = rz;
+    if (!ok) {
+      // flag the field; wait (bounded, 1 s) for every copy still in flight
+      // before the block's shared memory is released
+      if (tid == 0 && st) atomicExch(&st->fault, 1);
+      for (int q = 0; q < 4; ++q)
+        if ((pending >> q) & 1u) mbar_wait_bounded(smem_u32(&bars[q]), (ph >> q) & 1u, 1000000000ull);
+      __syncthreads();
+    } else {
+      acc[0] = rz;
+    }
   }
   if (a.ndots) block_finish(a, acc, f, act);
 }

@@ -184,3 +184,22 @@ def test_zero_and_breakdown_rules():
     assert res.iterations == 0 and res.status == oracle.STATUS_OK     # G 1 = 1: r_0 = 0
     res = oracle.preconditioned_cg(z, 0.1, tol=0.0, maxit=3)
     assert res.iterations == 0
+
+
+@pytest.mark.parametrize("shape,gamma", [((32, 48), 0.01), ((16, 12, 8), 0.1)])
+def test_spectral_space_iterates_equal_physical(shape, gamma):
+    """M is circulant, so in spectral space it is the pointwise multiply by
+    M_hat: the iterates, histories and pass counts equal the physical-space
+    ones in float64 (to rounding)."""
+    if len(shape) == 3:
+        u = fields.random_velocity_field(shape, 1, fields.spectrum_3d_kolmogorov)[0]
+    else:
+        u = fields.random_scalar_field(shape, 1, fields.spectrum_2d_kraichnan)
+    ub = oracle.filter_field(u, gamma)
+    a = oracle.preconditioned_cg(ub, gamma, tol=0.0, maxit=6)
+    b = oracle.preconditioned_cg(ub, gamma, tol=0.0, maxit=6, space="spectral")
+    np.testing.assert_allclose(b.u, a.u, atol=1e-12 * np.abs(a.u).max())
+    np.testing.assert_allclose(b.history, a.history, rtol=1e-9)
+    c = oracle.solve("pcg", ub, gamma, tol=1e-9, maxit=100, space="spectral")
+    d = oracle.solve("pcg", ub, gamma, tol=1e-9, maxit=100)
+    assert c.iterations == d.iterations and c.status == d.status == oracle.STATUS_OK
