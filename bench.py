@@ -459,7 +459,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "cg", "vancittert", "sd"])
+    ap.add_argument("--method", default="bicgstab", choices=["bicgstab", "cg", "vancittert", "sd", "pcg"])
     ap.add_argument("--no-extras", action="store_true", help="skip the comparison methods and CPU baseline")
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the iteration loop from the host instead of a graph while node (same kernels; "
