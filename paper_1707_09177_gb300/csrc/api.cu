@@ -1122,6 +1122,7 @@ ad_status get_cnn(ad_ctx* ctx, const ad_grid* g, int B, bool training, CnnWork**
         (s = cnn_alloc(ctx, cw, (void**)&w.frag3, frag)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.frag2t, frag)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.frag3t, frag)) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.frag4, sizeof(uint2) * 27 * 2 * 32)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.H1, act)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.H2, act)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.H3, act)) != AD_OK ||
@@ -1549,7 +1550,7 @@ ad_status ad_guess_infer(ad_ctx* ctx, const ad_grid* grid, const float* weights,
   CK(cnn_pack(cw->w, st));
   CK(cnn_forward(cw->w, ubar, u0, nullptr, (int)grid->n[0], (int)grid->n[1], (int)grid->n[2], batch,
                  cnn_ascale(grid->gamma), st));
-  ctx->launches = 4 + 5 + 1;
+  ctx->launches = 5 + 5 + 1;
   return AD_OK;
 }
 

@@ -7,9 +7,10 @@
 // Activations are bfloat16, channels-last: H[b][p][32], p = (z*Y + y)*X + x.
 // The 32 -> 32 layers are implicit GEMMs on the tensor cores (bf16 inputs,
 // float32 accumulation): for an x-segment of 32 points per warp, the product
-// over K = 27 taps x 32 input channels into N = 32 output channels. The 1-channel
-// first and last layers run on the CUDA cores (the first one in float32, so the
-// small differences it forms from u_bar are not lost to bfloat16 rounding). The
+// over K = 27 taps x 32 input channels into N = 32 output channels; the 32 -> 1
+// last layer is the same GEMM with one n8 tile (column 0). The 1 -> 32 first
+// layer runs on the CUDA cores in float32, so the small differences it forms
+// from u_bar are not lost to bfloat16 rounding. The
 // output is scaled by the fixed factor A = (delta/h)^2 = 1/(pi gamma)^2, the
 // grid-unit weight of the Laplacian in G^{-1} = I - delta^2 Laplacian (Eq. df):
 // u0 = u_bar + sigma * A * y. Training keeps float32 master
@@ -84,13 +85,40 @@ __device__ __forceinline__ void load_row(unsigned char* dst, const __nv_bfloat16
   }
 }
 
+// Asynchronous form of load_row for the three rows (b = 0..2) of z offset a:
+// 16-byte cp.async copies into `dst` (3 rows of TX + 2 points, ROWB bytes per
+// point), committed as one group by the caller.
+__device__ __forceinline__ void stage_rows_async(unsigned char* dst, const __nv_bfloat16* H, long long base, int z,
+                                                 int y, int a, int X, int Y, int Z, int x0, int TX, int tid,
+                                                 int nthr) {
+  const int n16 = (TX + 2) * 4;
+  for (int bb = 0; bb < 3; ++bb) {
+    const long long rowbase = base + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
+    unsigned char* row = dst + bb * (TX + 2) * ROWB;
+    for (int i = tid; i < n16; i += nthr) {
+      const int pt = i >> 2, q = i & 3;
+      const int x = wrap(x0 - 1 + pt, X);
+      const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(row + pt * ROWB + q * 16));
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(H + (rowbase + x) * C + q * 8)
+                   : "memory");
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // 32 -> 32 convolution on the tensor cores. One warp computes 32 consecutive
 // x points (two m16 tiles) x 32 output channels (four n8 tiles); a block holds
 // TX/32 warps over an x-segment of TX points of one (b, z, y) row and stages
-// the neighbour rows (periodic) in shared memory, three at a time. Weights come in mma
+// the neighbour rows (periodic) in shared memory, three at a time, the next three
+// copied (cp.async) while the current ones are in use. Weights come in mma
 // B-fragment order (see k_pack_frag) from global memory (L1-resident).
 // mode 0: out = bf16(relu(acc));  mode 1: out = bf16(acc * (mask > 0)).
 __global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16* __restrict__ Hin,
@@ -119,17 +147,22 @@ __global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16* __restric
   // i + 8*(mi & 1), channel offset 8*(mi >> 1)
   const int mi = lane >> 3, li = lane & 7;
   const int prow = li + 8 * (mi & 1), coff = 16 * (mi >> 1);
+  // the three rows of z offset a + 1 are copied (cp.async) into the other
+  // half of shared memory while the taps of offset a run on the tensor cores
+  const int hstride = 3 * (TX + 2) * ROWB;   // bytes of one half
+  stage_rows_async(sm, Hin, base, z, y, 0, X, Y, Z, x0, TX, tid, nthr);
   for (int ab = 0; ab < 9; ++ab) {
-    if (ab % 3 == 0) {               // stage the three rows (a, b = 0..2) of this z offset
+    if (ab % 3 == 0) {
       const int a = ab / 3;
-      __syncthreads();
-      for (int bb = 0; bb < 3; ++bb) {
-        const long long rowbase = base + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
-        load_row(sm + bb * (TX + 2) * ROWB, Hin, rowbase, X, x0, TX, tid, nthr);
+      if (a < 2) {
+        stage_rows_async(sm + ((a + 1) & 1) * hstride, Hin, base, z, y, a + 1, X, Y, Z, x0, TX, tid, nthr);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
       }
       __syncthreads();
     }
-    const unsigned char* rowt = sm + (ab % 3) * (TX + 2) * ROWB;
+    const unsigned char* rowt = sm + ((ab / 3) & 1) * hstride + (ab % 3) * (TX + 2) * ROWB;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
       const int tap = ab * 3 + c;
@@ -150,6 +183,7 @@ __global__ void __launch_bounds__(128) k_conv_mma(const __nv_bfloat16* __restric
         }
       }
     }
+    if (ab % 3 == 2) __syncthreads();  // this half is refilled two offsets later
   }
   // epilogue: C fragment (row g / g+8, cols 2t, 2t+1)
   const int g = lane >> 2, t = lane & 3;
@@ -294,6 +328,19 @@ __global__ void k_pack_frag(const float* __restrict__ W, uint2* __restrict__ Wf,
   Wf[i] = make_uint2(pack_bf16(Bv(2 * t, g), Bv(2 * t + 1, g)), pack_bf16(Bv(2 * t + 8, g), Bv(2 * t + 9, g)));
 }
 
+// Packs the layer-4 weights W4[tap][ci] as the B fragments of one n8 tile
+// whose column 0 holds them and columns 1..7 are zero:
+// Wf[(tap*2 + ks)*32 + lane] = {B(2t, g), B(2t+1, g)}, {B(2t+8, g), B(2t+9, g)},
+// B(k, j) = (j == 0) ? W4[tap][16 ks + k] : 0.
+__global__ void k_pack_frag4(const float* __restrict__ W4, uint2* __restrict__ Wf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= TAPS * 2 * 32) return;
+  const int lane = i & 31, ks = (i >> 5) & 1, tap = i >> 6;
+  const int g = lane >> 2, t = lane & 3;
+  auto Bv = [&](int k) { return g == 0 ? W4[tap * C + ks * 16 + k] : 0.f; };
+  Wf[i] = make_uint2(pack_bf16(Bv(2 * t), Bv(2 * t + 1)), pack_bf16(Bv(2 * t + 8), Bv(2 * t + 9)));
+}
+
 // sum of squares of each sample (float64 partials per block, then per sample)
 __global__ void k_sumsq(const float* __restrict__ u, long long P, double* __restrict__ out) {
   const int b = blockIdx.y;
@@ -351,65 +398,103 @@ __global__ void __launch_bounds__(256) k_conv_in(const float* __restrict__ ubar,
   }
 }
 
-// Layer 4 and the residual output: u0 = u_bar + sigma * A * sum_{tap, ci} W4[tap][ci] H3[p + off][ci].
-// With utrue != nullptr it also writes g = sigma * A * 2 (u0 - u_true) / ||u_true||^2 / B (the
-// gradient of the batch-mean loss with respect to the layer-4 output) and accumulates
-// sum (u0 - u_true)^2 / ||u_true||^2 / B into loss.
-__global__ void __launch_bounds__(256) k_conv_out(const __nv_bfloat16* __restrict__ H3, const float* __restrict__ W4,
-                                                  const float* __restrict__ ubar, const double* __restrict__ sumsq,
-                                                  float* __restrict__ u0, const float* __restrict__ utrue,
-                                                  const double* __restrict__ tsumsq, float* __restrict__ gout,
-                                                  double* __restrict__ loss, int X, int Y, int Z, int B,
-                                                  double ascale) {
-  const long long P = (long long)X * Y * Z;
+// Layer 4 (32 -> 1) on the tensor cores and the residual output:
+//   u0 = u_bar + sigma * A * sum_{tap, ci} W4[tap][ci] H3[p + off][ci].
+// The same implicit GEMM as k_conv_mma with one n8 tile whose column 0 holds
+// W4 (bf16, the other seven columns zero): the neighbour rows are staged in
+// shared memory once per block and read by ldmatrix, instead of each thread
+// gathering its 27 x 32 inputs from L1. Column 0 of the accumulator lives in
+// the lanes with lane % 4 == 0 (rows g and g + 8 of each m16 tile).
+// With utrue != nullptr it also writes g = sigma * A * 2 (u0 - u_true) /
+// ||u_true||^2 / B and accumulates sum (u0 - u_true)^2 / ||u_true||^2 / B
+// into loss.
+__global__ void __launch_bounds__(128) k_conv_out_mma(const __nv_bfloat16* __restrict__ H3,
+                                                      const uint2* __restrict__ Wf, const float* __restrict__ ubar,
+                                                      const double* __restrict__ sumsq, float* __restrict__ u0,
+                                                      const float* __restrict__ utrue,
+                                                      const double* __restrict__ tsumsq, float* __restrict__ gout,
+                                                      double* __restrict__ loss, int X, int Y, int Z, int B, int TX,
+                                                      double ascale) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ double red[4];
+  const int tid = threadIdx.x, nthr = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const int segs = X / TX;
+  int r = blockIdx.x;
+  const int seg = r % segs;
+  r /= segs;
+  const int y = r % Y, z = r / Y;
   const int b = blockIdx.y;
-  __shared__ float w[TAPS * C];
-  for (int i = threadIdx.x; i < TAPS * C; i += blockDim.x) w[i] = W4[i];
-  __syncthreads();
+  const int x0 = seg * TX;
+  const long long P = (long long)X * Y * Z;
+  const long long base = (long long)b * P;
+  float acc[2][4];
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[m][e] = 0.f;
+  const int mi = lane >> 3, li = lane & 7;
+  const int prow = li + 8 * (mi & 1), coff = 16 * (mi >> 1);
+  const int hstride = 3 * (TX + 2) * ROWB;   // bytes of one half
+  stage_rows_async(sm, H3, base, z, y, 0, X, Y, Z, x0, TX, tid, nthr);
+  for (int ab = 0; ab < 9; ++ab) {
+    if (ab % 3 == 0) {
+      const int a = ab / 3;
+      if (a < 2) {
+        stage_rows_async(sm + ((a + 1) & 1) * hstride, H3, base, z, y, a + 1, X, Y, Z, x0, TX, tid, nthr);
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      __syncthreads();
+    }
+    const unsigned char* rowt = sm + ((ab / 3) & 1) * hstride + (ab % 3) * (TX + 2) * ROWB;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const int tap = ab * 3 + c;
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        uint32_t af[2][4];
+#pragma unroll
+        for (int m = 0; m < 2; ++m) {
+          const int pt = warp * 32 + m * 16 + prow + c;
+          ldsm_x4(af[m], rowt + pt * ROWB + ks * 32 + coff);
+        }
+        const uint2 bw = __ldg(Wf + (tap * 2 + ks) * 32 + lane);
+        const uint32_t bf[2] = {bw.x, bw.y};
+        mma_bf16(acc[0], af[0], bf);
+        mma_bf16(acc[1], af[1], bf);
+      }
+    }
+    if (ab % 3 == 2) __syncthreads();  // this half is refilled two offsets later
+  }
+  const int g = lane >> 2, t = lane & 3;
   const double sigma = sqrt(fmax(sumsq[b] / (double)P, 1e-300)) * ascale;   // sigma * A
+  const long long rowp = base + ((long long)z * Y + y) * X + x0 + warp * 32;
   double lsum = 0.0;
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
-    float s = 0.f;
-    for (int a = 0; a < 3; ++a)
-      for (int bb = 0; bb < 3; ++bb) {
-        const long long row = (long long)b * P + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
-        for (int c = 0; c < 3; ++c) {
-          const int t = (a * 3 + bb) * 3 + c;
-          const uint4* src = reinterpret_cast<const uint4*>(H3 + (row + wrap(x + c - 1, X)) * C);
+  if (t == 0) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const uint4 v = src[q];
-            const uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+    for (int m = 0; m < 2; ++m)
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-              const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162*>(&wds[k]);
-              const int ci = q * 8 + 2 * k;
-              s = fmaf(w[t * C + ci], __bfloat162float(h.x), s);
-              s = fmaf(w[t * C + ci + 1], __bfloat162float(h.y), s);
-            }
-          }
+      for (int h = 0; h < 2; ++h) {
+        const long long gi = rowp + m * 16 + g + 8 * h;
+        const float uo = ubar[gi] + (float)sigma * acc[m][2 * h];
+        u0[gi] = uo;
+        if (utrue) {
+          const double d = (double)uo - (double)utrue[gi];
+          const double inv = 1.0 / (tsumsq[b] * (double)B);
+          lsum += d * d * inv;
+          gout[gi] = (float)(sigma * 2.0 * d * inv);
         }
       }
-    const long long gi = (long long)b * P + p;
-    const float uo = ubar[gi] + (float)sigma * s;
-    u0[gi] = uo;
-    if (utrue) {
-      const double d = (double)uo - (double)utrue[gi];
-      const double inv = 1.0 / (tsumsq[b] * (double)B);
-      lsum += d * d * inv;
-      gout[gi] = (float)(sigma * 2.0 * d * inv);
-    }
   }
   if (utrue) {
     for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-    __shared__ double red[32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+    if (lane == 0) red[warp] = lsum;
     __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[w2];
-      atomicAdd(loss, t);
+    if (tid == 0) {
+      double tt = 0.0;
+      for (int w2 = 0; w2 < (nthr >> 5); ++w2) tt += red[w2];
+      atomicAdd(loss, tt);
     }
   }
 }
@@ -582,7 +667,8 @@ __global__ void k_adam(float* __restrict__ w, float* __restrict__ m, float* __re
 
 int cnn_tile(int X) { return X % 64 == 0 ? 64 : 32; }
 
-size_t cnn_conv_smem(int X) { return (size_t)3 * (cnn_tile(X) + 2) * ROWB; }
+// two halves of three staged rows each (double-buffered z offsets)
+size_t cnn_conv_smem(int X) { return (size_t)2 * 3 * (cnn_tile(X) + 2) * ROWB; }
 
 bool cnn_shape_ok(int X, int Y, int Z) { return X % 32 == 0 && Y >= 3 && Z >= 3; }
 
@@ -604,8 +690,12 @@ cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const
   const dim3 gc((unsigned)(X / TX) * Y * Z, B);
   k_conv_mma<<<gc, TX, sm, s>>>(w.H1, w.frag2, w.H2, nullptr, X, Y, Z, TX, 0);
   k_conv_mma<<<gc, TX, sm, s>>>(w.H2, w.frag3, w.H3, nullptr, X, Y, Z, TX, 0);
-  k_conv_out<<<gp, 256, 0, s>>>(w.H3, w.master + kW4, ubar, w.sumsq, u0, utrue, w.sumsq + B, w.g, w.sumsq + 2 * B,
-                                X, Y, Z, B, ascale);
+  if (sm > 48 * 1024) {
+    e = cudaFuncSetAttribute(k_conv_out_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_conv_out_mma<<<gc, TX, sm, s>>>(w.H3, w.frag4, ubar, w.sumsq, u0, utrue, w.sumsq + B, w.g, w.sumsq + 2 * B,
+                                    X, Y, Z, B, TX, ascale);
   return cudaGetLastError();
 }
 
@@ -615,6 +705,7 @@ cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s) {
   k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW3, w.frag3, 0);
   k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW2, w.frag2t, 1);
   k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW3, w.frag3t, 1);
+  k_pack_frag4<<<(TAPS * 2 * 32 + 255) / 256, 256, 0, s>>>(w.master + kW4, w.frag4);
   return cudaGetLastError();
 }
 

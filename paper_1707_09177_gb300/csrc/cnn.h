@@ -26,6 +26,7 @@ struct CnnBuffers {
   uint2* frag3 = nullptr;
   uint2* frag2t = nullptr;     // flipped, channel-swapped (backward data)
   uint2* frag3t = nullptr;
+  uint2* frag4 = nullptr;      // layer 4 weights as one n8 tile (column 0) in mma fragment order
   __nv_bfloat16* H1 = nullptr; // activations [B][P][32]
   __nv_bfloat16* H2 = nullptr;
   __nv_bfloat16* H3 = nullptr;

@@ -340,9 +340,11 @@ template <typename T> __device__ __forceinline__ void st2(T* p, T a, T b) {
 // the filter pass too although it keeps two FFT stages' worth of state live;
 // a few spilled words cost less than the latency the extra warps hide
 // (measured: the filter pass 28-31% faster than at 2 blocks and 128
-// registers, the x/y passes 5-17% faster than at 3 blocks and 80).
-#define GAD_BOUNDS(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 4 : 2)
-#define GAD_BOUNDS_FILT(T, E) __launch_bounds__(256, (sizeof(T) == 4 && (E) == 16) ? 4 : 2)
+// registers, the x/y passes 5-17% faster than at 3 blocks and 80). Float32,
+// E = 24 (radix-3 lengths): 3 blocks per SM (14-15% faster per pass than 2 at
+// 384^3 and 1536^2). Float64: 2 blocks.
+#define GAD_BOUNDS(T, E) __launch_bounds__(256, sizeof(T) == 4 ? ((E) == 16 ? 4 : 3) : 2)
+#define GAD_BOUNDS_FILT(T, E) __launch_bounds__(256, sizeof(T) == 4 ? ((E) == 16 ? 4 : 3) : 2)
 
 // ---------------------------------------------------------------------------
 // Row-tile streaming for the fused Krylov prologue/epilogue of the x passes.
