@@ -360,40 +360,60 @@ __global__ void k_sumsq(const float* __restrict__ u, long long P, double* __rest
   }
 }
 
-// Layer 1: H1[p][co] = relu(sum_tap W1[tap][co] * x0[p + off(tap)]), x0 = u_bar / sigma.
+// Layer 1: H1[p][co] = relu(sum_tap W1[tap][co] * x0[p + off(tap)]), x0 = u_bar / sigma,
+// in float32 on the CUDA cores. A thread computes two consecutive x points:
+// their 27 taps share the 9 neighbour rows, from which it loads the four
+// values x-1 .. x+2 once; the weights of eight output channels are read as
+// two float4 from shared memory and applied to both points.
 __global__ void __launch_bounds__(256) k_conv_in(const float* __restrict__ ubar, const double* __restrict__ sumsq,
                                                  const float* __restrict__ W1, __nv_bfloat16* __restrict__ H1,
                                                  int X, int Y, int Z) {
   const long long P = (long long)X * Y * Z;
+  const long long P2 = P >> 1;                       // point pairs (X is even)
   const int b = blockIdx.y;
-  __shared__ float w[TAPS * C];
+  __shared__ __align__(16) float w[TAPS * C];
   for (int i = threadIdx.x; i < TAPS * C; i += blockDim.x) w[i] = W1[i];
   __syncthreads();
   const float inv_sigma = (float)(1.0 / sqrt(fmax(sumsq[b] / (double)P, 1e-300)));
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  for (long long pp = blockIdx.x * (long long)blockDim.x + threadIdx.x; pp < P2;
+       pp += (long long)gridDim.x * blockDim.x) {
+    const long long p = 2 * pp;
     const int x = (int)(p % X), y = (int)((p / X) % Y), z = (int)(p / ((long long)X * Y));
-    float in[TAPS];
+    float v[9][4];                                   // row (a, b), x - 1 .. x + 2
+#pragma unroll
     for (int a = 0; a < 3; ++a)
+#pragma unroll
       for (int bb = 0; bb < 3; ++bb) {
         const long long row = (long long)b * P + ((long long)wrap(z + a - 1, Z) * Y + wrap(y + bb - 1, Y)) * X;
-        for (int c = 0; c < 3; ++c) in[(a * 3 + bb) * 3 + c] = ubar[row + wrap(x + c - 1, X)] * inv_sigma;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[a * 3 + bb][c] = ubar[row + wrap(x + c - 1, X)] * inv_sigma;
       }
-    uint4* dst = reinterpret_cast<uint4*>(H1 + ((long long)b * P + p) * C);
+    uint4* dst0 = reinterpret_cast<uint4*>(H1 + ((long long)b * P + p) * C);
+    uint4* dst1 = dst0 + 4;
 #pragma unroll 1
-    for (int q = 0; q < 4; ++q) {
-      uint32_t ow[4];
+    for (int q = 0; q < 4; ++q) {                    // output channels 8q .. 8q + 7
+      float s0[8], s1[8];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int co = q * 8 + 2 * k;
-        float s0 = 0.f, s1 = 0.f;
+      for (int k = 0; k < 8; ++k) s0[k] = s1[k] = 0.f;
 #pragma unroll
-        for (int t = 0; t < TAPS; ++t) {
-          s0 = fmaf(w[t * C + co], in[t], s0);
-          s1 = fmaf(w[t * C + co + 1], in[t], s1);
+      for (int r = 0; r < 9; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const int t = r * 3 + c;
+          const float4 wa = w4[t * 8 + 2 * q], wb = w4[t * 8 + 2 * q + 1];
+          const float i0 = v[r][c], i1 = v[r][c + 1];
+          const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            s0[k] = fmaf(wv[k], i0, s0[k]);
+            s1[k] = fmaf(wv[k], i1, s1[k]);
+          }
         }
-        ow[k] = pack_bf16(fmaxf(s0, 0.f), fmaxf(s1, 0.f));
-      }
-      dst[q] = make_uint4(ow[0], ow[1], ow[2], ow[3]);
+      dst0[q] = make_uint4(pack_bf16(fmaxf(s0[0], 0.f), fmaxf(s0[1], 0.f)), pack_bf16(fmaxf(s0[2], 0.f), fmaxf(s0[3], 0.f)),
+                           pack_bf16(fmaxf(s0[4], 0.f), fmaxf(s0[5], 0.f)), pack_bf16(fmaxf(s0[6], 0.f), fmaxf(s0[7], 0.f)));
+      dst1[q] = make_uint4(pack_bf16(fmaxf(s1[0], 0.f), fmaxf(s1[1], 0.f)), pack_bf16(fmaxf(s1[2], 0.f), fmaxf(s1[3], 0.f)),
+                           pack_bf16(fmaxf(s1[4], 0.f), fmaxf(s1[5], 0.f)), pack_bf16(fmaxf(s1[6], 0.f), fmaxf(s1[7], 0.f)));
     }
   }
 }
