@@ -294,26 +294,26 @@ __device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, boo
 
 // ---------------------------------------------------------------------------
 // Loads a W x n tile stored transposed in global memory (element (w, i) at
-// g[i*gstride + w]) into the shared-memory rows, U independent loads per
-// thread in flight.
-template <typename C, int U>
+// g[i*gstride + w]) into the shared-memory rows with asynchronous copies
+// (cp.async, one per complex element): every copy of the tile is in flight
+// at once without holding registers. Ends with the copies complete and a
+// barrier.
+template <typename C>
 __device__ __forceinline__ void load_transposed(C* s, int ld, const C* __restrict__ g, long long gstride, int W,
                                                 int n, int tid, int nthr) {
   const int lw = __ffs(W) - 1;
   const int total = W * n;
-  for (int base = tid; base < total; base += nthr * U) {
-    C tmp[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * nthr;
-      if (idx < total) tmp[u] = g[(long long)(idx >> lw) * gstride + (idx & (W - 1))];
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int idx = base + u * nthr;
-      if (idx < total) s[(idx & (W - 1)) * ld + phys(idx >> lw)] = tmp[u];
-    }
+  for (int idx = tid; idx < total; idx += nthr) {
+    const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(s + (idx & (W - 1)) * ld + phys(idx >> lw)));
+    const C* src = g + (long long)(idx >> lw) * gstride + (idx & (W - 1));
+    if constexpr (sizeof(C) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+    else
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
 }
 
 // Stores the shared-memory rows transposed (element (w, i) to g[i*gstride + w]).
@@ -730,8 +730,7 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
   if (act) {
     const long long base = (long long)f * a.P + (long long)row0 * nx;
     const C* S1 = reinterpret_cast<const C*>(a.S1) + (long long)f * a.SP + (long long)z * a.kxn * a.ny + y0;
-    load_transposed<C, 8>(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
-    __syncthreads();
+    load_transposed(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
     const C* twx = reinterpret_cast<const C*>(a.twx);
     const int h1 = (M >> 1) + 1;
     for (int idx = tid; idx < a.W * h1; idx += nthr) {
@@ -895,8 +894,7 @@ __global__ void GAD_BOUNDS(T, E) k_yinv(PassArgs<T> a) {
   const int zt = a.nz / a.W;
   const int kx = blockIdx.x / zt, z0 = (blockIdx.x - kx * zt) * a.W;
   const C* S2 = reinterpret_cast<const C*>(a.S2) + (long long)f * a.SP + (long long)kx * L * a.nz + z0;
-  load_transposed<C, 8>(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
-  __syncthreads();
+  load_transposed(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
   C* S1 = reinterpret_cast<C*>(a.S1) + (long long)f * a.SP;
   const int kxn = a.kxn;
   auto emit = [&](int w, int i, const C& x) { S1[((long long)(z0 + w) * kxn + kx) * L + i] = x; };
