@@ -47,6 +47,12 @@ struct Acc {
 
 template <typename T> struct V4 { T v[4]; };
 
+// G_hat(k) = k_c^2/(k_c^2 + |k|^2). float32: reciprocal-based quotient
+// (__fdividef, within 2 ulp; the spectra are stored in float32 anyway);
+// float64: IEEE division.
+__device__ __forceinline__ float ghat(float kc2, float k2) { return __fdividef(kc2, kc2 + k2); }
+__device__ __forceinline__ double ghat(double kc2, double k2) { return kc2 / (kc2 + k2); }
+
 __device__ __forceinline__ V4<float> ld4(const float* p) {
   float4 a = *reinterpret_cast<const float4*>(p);
   return {{a.x, a.y, a.z, a.w}};
@@ -816,22 +822,30 @@ __global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
     auto load = [&](int w, int i) -> C {
       return w < nvalid ? S[(long long)w * L + i] : C{T(0), T(0)};
     };
+    // the sequence's part of |k|^2 and its Parseval weight, recomputed only
+    // when the sequence changes (a butterfly's R elements share it)
+    int cw = -1, ck2 = 0;
+    T cwgt = T(0);
     auto mul = [&](int w, int i, C& X) {
-      const int seq = seq0 + w;
-      int kx, k2i;
-      const int ki = i < half ? i : i - L;
-      if (three_d) {
-        kx = seq / ny;
-        const int kyi = seq - kx * ny;
-        const int ky = kyi < (ny >> 1) ? kyi : kyi - ny;
-        k2i = kx * kx + ky * ky + ki * ki;
-      } else {
-        kx = seq;
-        k2i = kx * kx + ki * ki;
+      if (w != cw) {
+        cw = w;
+        const int seq = seq0 + w;
+        int kx;
+        if (three_d) {
+          kx = seq / ny;
+          const int kyi = seq - kx * ny;
+          const int ky = kyi < (ny >> 1) ? kyi : kyi - ny;
+          ck2 = kx * kx + ky * ky;
+        } else {
+          kx = seq;
+          ck2 = kx * kx;
+        }
+        cwgt = (kx == 0 || kx == nxh) ? T(1) : T(2);
       }
-      const T g = kc2 / (kc2 + T(k2i));
+      const int ki = i < half ? i : i - L;
+      const T g = ghat(kc2, T(ck2 + ki * ki));
       if (op != FI_NONE && w < nvalid) {
-        const T wgt = (kx == 0 || kx == nxh) ? T(1) : T(2);
+        const T wgt = cwgt;
         const T m2 = X.x * X.x + X.y * X.y;
         const T wm = wgt * m2;
         if (op == FI_XGX) {

@@ -66,12 +66,6 @@ __global__ void GAD_BOUNDS(T, E) k_linv(PassArgs<T> a) {
   fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, load, emit, false, false);
 }
 
-// G_hat(k) = k_c^2/(k_c^2 + |k|^2). float32: reciprocal-based quotient
-// (__fdividef, within 2 ulp; the spectra are stored in float32 anyway);
-// float64: IEEE division.
-__device__ __forceinline__ float ghat(float kc2, float k2) { return __fdividef(kc2, kc2 + k2); }
-__device__ __forceinline__ double ghat(double kc2, double k2) { return kc2 / (kc2 + k2); }
-
 __device__ __forceinline__ float sinpi_t(float x) { return sinpif(x); }
 __device__ __forceinline__ double sinpi_t(double x) { return sinpi(x); }
 
