@@ -1875,6 +1875,12 @@ ad_status ad_curl(ad_ctx* ctx, const ad_grid* grid, int nvel, const void* u, voi
   if (nvel == 0) { ctx->launches = 0; return AD_OK; }
   if (!u || !omega) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
   if (((uintptr_t)u | (uintptr_t)omega) & 15) return fail(ctx, AD_ERR_ARG, "field pointers must be 16-byte aligned");
+  {
+    const size_t es = grid->dtype == AD_F64 ? 8 : 4;
+    const long long P = grid->n[0] * grid->n[1] * (grid->ndim == 3 ? grid->n[2] : 1);
+    if (overlaps(omega, (size_t)nvel * nout * P * es, u, (size_t)nvel * ncomp * P * es))
+      return fail(ctx, AD_ERR_ARG, "omega must not overlap u");
+  }
   CK(cudaSetDevice(ctx->device));
   Plan *pin = nullptr, *pout = nullptr;
   if ((s = get_plan(ctx, grid, nvel * ncomp, &pin)) != AD_OK) return s;

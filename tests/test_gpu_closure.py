@@ -168,6 +168,12 @@ def test_curl(gad, shape, dtype):
         assert _rel(got, ref) < tol
 
 
+def test_curl_rejects_overlap(gad):
+    big = _to_gpu(np.zeros((3, 32, 32), dtype=np.float32))
+    with pytest.raises(gad.GadError):
+        gad.curl(big[:2], ndim=2, out=big[1])
+
+
 def test_curl_of_a_single_mode(gad):
     n = 32
     x = 2 * np.pi * np.arange(n) / n
