@@ -138,6 +138,7 @@ struct ad_ctx {
   void* stat_buf = nullptr;                   // device scratch of the statistics calls
   size_t stat_cap = 0;
   unsigned long long wait_ns = 1000000000ull; // limit of bounded device waits
+  int rev_next = 0;                           // field order of the next pass launch
 };
 
 namespace {
@@ -539,8 +540,15 @@ template <typename T> void store_args(LaunchRec& r, const PassArgs<T>& a);
 template <> void store_args<float>(LaunchRec& r, const PassArgs<float>& a) { r.af = a; r.f64 = false; }
 template <> void store_args<double>(LaunchRec& r, const PassArgs<double>& a) { r.ad = a; r.f64 = true; }
 
+// Successive pass launches alternate the order of the fields (PassArgs::rev):
+// a pass then starts on the fields the previous one finished with, whose
+// vectors and spectra may still be in L2. A field's result does not depend on
+// the order.
 template <typename T>
-cudaError_t issue(ad_ctx* ctx, int kind, const PassCfg& pc, cudaStream_t s, const PassArgs<T>& a) {
+cudaError_t issue(ad_ctx* ctx, int kind, const PassCfg& pc, cudaStream_t s, const PassArgs<T>& a0) {
+  PassArgs<T> a = a0;
+  a.rev = ctx->rev_next;
+  ctx->rev_next ^= 1;
   if (ctx->record) {
     LaunchRec r;
     r.kind = kind; r.E = pc.E; r.grid = pc.grid; r.threads = block_threads(pc); r.smem = pc.smem;

@@ -96,6 +96,7 @@ struct PassArgs {
   int pair_code;             // closure: pair p = (i, j) at bits 4p (i) and 4p + 2 (j)
   unsigned long long wait_ns;  // limit of a bounded device wait (0: give up at once)
   int chunk;                 // preconditioner stencil: positions of the march axis per block
+  int rev;                   // fields in reverse launch order: field f = gridDim.y - 1 - blockIdx.y
   void* S1;
   void* S2;
   const T* A;

@@ -47,6 +47,14 @@ struct Acc {
 
 template <typename T> struct V4 { T v[4]; };
 
+// Field of this block. Successive passes alternate the order in which the
+// fields' blocks are launched (rev), so that each pass starts on the fields
+// whose data the previous pass touched last and may still find in L2.
+template <typename A>
+__device__ __forceinline__ int field_of(const A& a) {
+  return a.rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
+}
+
 // G_hat(k) = k_c^2/(k_c^2 + |k|^2). float32: reciprocal-based quotient
 // (__fdividef, within 2 ulp; the spectra are stored in float32 anyway);
 // float64: IEEE division.
@@ -501,8 +509,8 @@ __device__ __forceinline__ void xfwd_prologue(const PassArgs<T>& a, typename cpx
     }
     case XF_MUL: {                                // closure: x = A_i A_j
       long long oi, oj;
-      pair_offsets(a, (int)blockIdx.y, oi, oj);
-      const long long fb = (long long)blockIdx.y * a.P;
+      pair_offsets(a, field_of(a), oi, oj);
+      const long long fb = (long long)field_of(a) * a.P;
       auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + (g - fb) + oi); y_[u] = ld4(vA + (g - fb) + oj); };
       auto fin = [&](int u, int w, int q, long long) {
         V4<T> xo;
@@ -630,8 +638,8 @@ __device__ __forceinline__ void xinv_epilogue(const PassArgs<T>& a, const typena
     }
     case XI_TAU: {                                // closure: O1 = B_i B_j - y
       long long oi, oj;
-      pair_offsets(a, (int)blockIdx.y, oi, oj);
-      const long long fb = (long long)blockIdx.y * a.P;
+      pair_offsets(a, field_of(a), oi, oj);
+      const long long fb = (long long)field_of(a) * a.P;
       auto ldf = [&](int u, long long g) { b_[u] = ld4(vB + (g - fb) + oi); c_[u] = ld4(vB + (g - fb) + oj); };
       auto fin = [&](int u, int w, int q, long long g) {
         const V4<T> y = get_pair<T>(s + w * ld, q);
@@ -658,7 +666,7 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y;
+  const int f = field_of(a);
   if (a.clear_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
   FieldState* st = a.st ? a.st + f : nullptr;
   if (st && !st->active && !a.force) return;
@@ -724,7 +732,7 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y;
+  const int f = field_of(a);
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
@@ -800,7 +808,7 @@ __global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y;
+  const int f = field_of(a);
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
@@ -879,7 +887,7 @@ __global__ void GAD_BOUNDS(T, E) k_yfwd(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y;
+  const int f = field_of(a);
   if (a.st && !a.st[f].active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int L = a.ny;
@@ -901,7 +909,7 @@ __global__ void GAD_BOUNDS(T, E) k_yinv(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y;
+  const int f = field_of(a);
   if (a.st && !a.st[f].active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int L = a.ny;

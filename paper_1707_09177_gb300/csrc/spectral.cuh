@@ -24,7 +24,7 @@ __global__ void GAD_BOUNDS(T, E) k_lfwd(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y, tid = threadIdx.x;
+  const int f = field_of(a), tid = threadIdx.x;
   const int L = a.fft.L;
   const bool three_d = a.nz > 1;
   const int nseq = three_d ? a.kxn * a.ny : a.kxn;
@@ -46,7 +46,7 @@ __global__ void GAD_BOUNDS(T, E) k_linv(PassArgs<T> a) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = blockIdx.y, tid = threadIdx.x;
+  const int f = field_of(a), tid = threadIdx.x;
   const int L = a.fft.L;
   const bool three_d = a.nz > 1;
   const int nseq = three_d ? a.kxn * a.ny : a.kxn;
@@ -221,7 +221,7 @@ __device__ __forceinline__ void sp_store(const SpIn<T>& x, const T* vB, T* vO1, 
 // are summed with FMAs, and the pairs' sums are accumulated with TwoSum.
 template <typename T, int OP>
 __global__ void __launch_bounds__(256) k_spec(PassArgs<T> a) {
-  const int f = blockIdx.y, tid = threadIdx.x;
+  const int f = field_of(a), tid = threadIdx.x;
   if (a.clear_cond && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) cudaGraphSetConditional(a.cond, 0u);
   FieldState* st = a.st + f;
   const bool act = st->active != 0 || a.force;

@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(256) k_sten(PassArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bars[4];
   T* ring = reinterpret_cast<T*>(smem_raw);
-  const int f = blockIdx.y;
+  const int f = field_of(a);
   if (a.clear_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
