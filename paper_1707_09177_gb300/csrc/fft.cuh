@@ -176,12 +176,19 @@ __device__ __forceinline__ int run_stride(int st) {
 // memory (with the fused Krylov prologue/epilogue) for the first and last
 // stage. `mid_barrier` separates the loads from the writes when both touch
 // the same shared-memory tile.
-template <typename C, int E, int R, bool INV, class Load, class Emit>
+//
+// LRC and NSC, when nonzero, are L/R and ns as compile-time constants (powers
+// of two): the sequence and sub-transform indices become shifts and masks and
+// the shared-memory runs get immediate offsets. They must equal the plan's
+// values (fft_run_fixed checks the plan before taking that path).
+template <typename C, int E, int R, bool INV, int LRC = 0, int NSC = 0, class Load, class Emit>
 __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __restrict__ tw, int tid, int nthr,
                                          Load& load, Emit& emit, bool mid_barrier) {
   constexpr int NB = E / R;
   static_assert(NB * R == E, "radix must divide the per-thread element count");
-  const int lr = L / R;
+  static_assert((LRC & (LRC - 1)) == 0 && (NSC & (NSC - 1)) == 0, "constant strides are powers of two");
+  const int lr = LRC ? LRC : L / R;
+  const int ns = NSC ? NSC : sg.ns;
   C v[NB][R];
   int wrow[NB], jj[NB];
   const bool on = tid < nthr;     // threads beyond the FFT's thread count only join barriers
@@ -190,8 +197,14 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int bi = tid + b * nthr;
-      const int w = fquot(bi, sg.rcp_lr);
-      const int j = bi - w * lr;
+      int w, j;
+      if constexpr (LRC > 0) {
+        w = (int)((unsigned)bi / (unsigned)LRC);
+        j = (int)((unsigned)bi % (unsigned)LRC);
+      } else {
+        w = fquot(bi, sg.rcp_lr);
+        j = bi - w * lr;
+      }
       wrow[b] = w;
       jj[b] = j;
       if constexpr (is_rows<Load>::value) {
@@ -208,12 +221,14 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
   }
   if (mid_barrier) __syncthreads();
   if (on) {
-    const int est = is_rows<Emit>::value ? run_stride<R>(sg.ns) : 0;
+    const int est = is_rows<Emit>::value ? run_stride<R>(ns) : 0;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = jj[b];
-      const int k = j - sg.ns * fquot(j, sg.rcp_ns);
-      if (sg.ns > 1) {
+      int k;
+      if constexpr (NSC > 0) k = (int)((unsigned)j % (unsigned)NSC);
+      else k = j - ns * fquot(j, sg.rcp_ns);
+      if (ns > 1) {
         const int kt = k * sg.tw_step;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
@@ -232,7 +247,7 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
         }
       }
 #pragma unroll
-      for (int r = 0; r < R; ++r) emit(wrow[b], o + r * sg.ns, v[b][r]);
+      for (int r = 0; r < R; ++r) emit(wrow[b], o + r * ns, v[b][r]);
     }
   }
 }
@@ -244,12 +259,14 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
 // butterfly j (ns = 1, no twiddles), so the multiply happens in between.
 // `mul(w, i, x)` scales element i and may accumulate inner products;
 // `emit(w, i, x)` consumes the inverse stage's outputs (index j*R + r).
-template <typename C, int E, int R, class Load, class Mul, class Emit>
+// LRC as in stage_io.
+template <typename C, int E, int R, int LRC = 0, class Load, class Mul, class Emit>
 __device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C* __restrict__ tw, int tid, int nthr,
                                              Load& load, Mul& mul, Emit& emit, bool mid_barrier) {
   constexpr int NB = E / R;
   static_assert(NB * R == E, "radix must divide the per-thread element count");
-  const int lr = L / R;
+  static_assert((LRC & (LRC - 1)) == 0, "constant strides are powers of two");
+  const int lr = LRC ? LRC : L / R;
   C v[NB][R];
   int wrow[NB], jj[NB];
   const bool on = tid < nthr;
@@ -258,8 +275,14 @@ __device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C*
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int bi = tid + b * nthr;
-      const int w = fquot(bi, sg.rcp_lr);
-      const int j = bi - w * lr;
+      int w, j;
+      if constexpr (LRC > 0) {
+        w = (int)((unsigned)bi / (unsigned)LRC);
+        j = (int)((unsigned)bi % (unsigned)LRC);
+      } else {
+        w = fquot(bi, sg.rcp_lr);
+        j = bi - w * lr;
+      }
       wrow[b] = w;
       jj[b] = j;
       if constexpr (is_rows<Load>::value) {
@@ -280,7 +303,7 @@ __device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C*
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       const int j = jj[b];                  // k = j: ns = L/R exceeds every j
-      if (sg.ns > 1) {
+      if (lr > 1) {
         const int kt = j * sg.tw_step;
 #pragma unroll
         for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[r * kt]);
@@ -401,6 +424,125 @@ __device__ __forceinline__ void fft_filter_run(C* s, int ld, const FftPlan& fwd,
   if (n > 4) { stage_dispatch<C, E, true>(inv.L, inv.st[3], tw, tid, nthr, rows, rows, true); __syncthreads(); }
   const FftStage sl = stage_at(inv, n - 1);
   stage_dispatch<C, E, true>(inv.L, sl, tw, tid, nthr, rows, emit, false);
+}
+
+// --- fixed plans -----------------------------------------------------------
+// The plan the host builds for a power-of-two length L and E elements per
+// thread (balanced radices of at most 16 for E = 16, 8 otherwise), as
+// compile-time constants: stage q has radix rad(q) and follows sub-transforms
+// of size ns(q). REV lists the radices in reverse order (the filter pass's
+// inverse plan).
+__host__ __device__ constexpr int ct_log2(int L) { return L > 1 ? 1 + ct_log2(L >> 1) : 0; }
+
+template <int L, int E, bool REV>
+struct CtPlan {
+  static_assert(L > 1 && (L & (L - 1)) == 0, "fixed plans are for powers of two");
+  static constexpr int a = ct_log2(L);
+  static constexpr int maxlog = (E % 16 == 0) ? 4 : 3;
+  static constexpr int n = (a + maxlog - 1) / maxlog;
+  __host__ __device__ static constexpr int fwd_rad(int q) { return 1 << (a / n + (q < a % n ? 1 : 0)); }
+  __host__ __device__ static constexpr int rad(int q) { return REV ? fwd_rad(n - 1 - q) : fwd_rad(q); }
+  __host__ __device__ static constexpr int ns(int q) { return q == 0 ? 1 : ns(q - 1) * rad(q - 1); }
+};
+
+// True when plan p is exactly CtPlan<L, E, REV> (length, stage count and
+// every radix); the fixed path runs only then.
+template <int L, int E, bool REV>
+__device__ __forceinline__ bool ct_matches(const FftPlan& p) {
+  using P = CtPlan<L, E, REV>;
+  if (p.L != L || p.nst != P::n) return false;
+  bool ok = true;
+  if constexpr (P::n > 0) ok = ok && p.st[0].radix == P::rad(0);
+  if constexpr (P::n > 1) ok = ok && p.st[1].radix == P::rad(1);
+  if constexpr (P::n > 2) ok = ok && p.st[2].radix == P::rad(2);
+  if constexpr (P::n > 3) ok = ok && p.st[3].radix == P::rad(3);
+  if constexpr (P::n > 4) ok = ok && p.st[4].radix == P::rad(4);
+  return ok && P::n <= 5;
+}
+
+template <typename C, int E, bool INV, int L, bool REV, int Q, class Load, class Emit>
+__device__ __forceinline__ void ct_stage(const FftPlan& p, const C* __restrict__ tw, int tid, int nthr, Load& load,
+                                         Emit& emit, bool mid_barrier) {
+  using P = CtPlan<L, E, REV>;
+  constexpr int R = P::rad(Q);
+  if constexpr (E % R == 0)
+    stage_io<C, E, R, INV, L / R, P::ns(Q)>(L, stage_at(p, Q), tw, tid, nthr, load, emit, mid_barrier);
+}
+
+// fft_run for a plan known to be CtPlan<L, E, false>.
+template <typename C, int E, bool INV, int L, class Load, class Emit>
+__device__ __forceinline__ void fft_run_ct(C* s, int ld, const FftPlan& p, int tid, int nthr, Load& load, Emit& emit,
+                                           bool load_from_tile, bool emit_to_tile) {
+  using P = CtPlan<L, E, false>;
+  constexpr int n = P::n;
+  const C* tw = reinterpret_cast<const C*>(p.tw);
+  SmemRows<C> rows{s, ld};
+  if constexpr (n == 1) {
+    ct_stage<C, E, INV, L, false, 0>(p, tw, tid, nthr, load, emit, load_from_tile && emit_to_tile);
+    if (emit_to_tile) __syncthreads();
+  } else {
+    ct_stage<C, E, INV, L, false, 0>(p, tw, tid, nthr, load, rows, load_from_tile);
+    __syncthreads();
+    if constexpr (n > 2) { ct_stage<C, E, INV, L, false, 1>(p, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 3) { ct_stage<C, E, INV, L, false, 2>(p, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 4) { ct_stage<C, E, INV, L, false, 3>(p, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    ct_stage<C, E, INV, L, false, n - 1>(p, tw, tid, nthr, rows, emit, emit_to_tile);
+    if (emit_to_tile) __syncthreads();
+  }
+}
+
+// Runs fft_run's transform through the fixed plan of length L when p is that
+// plan (float32 tiles, E = 16) and returns true; returns false, having done
+// nothing, otherwise.
+template <typename C, int E, bool INV, int L, class Load, class Emit>
+__device__ __forceinline__ bool fft_run_fixed(C* s, int ld, const FftPlan& p, int tid, int nthr, Load& load,
+                                              Emit& emit, bool load_from_tile, bool emit_to_tile) {
+  if constexpr (E == 16 && sizeof(C) == 8) {
+    if (ct_matches<L, E, false>(p)) {
+      fft_run_ct<C, E, INV, L>(s, ld, p, tid, nthr, load, emit, load_from_tile, emit_to_tile);
+      return true;
+    }
+  }
+  return false;
+}
+
+// fft_filter_run for plans known to be CtPlan<L, E, false> (forward) and
+// CtPlan<L, E, true> (inverse).
+template <typename C, int E, int L, class Load, class Mul, class Emit>
+__device__ __forceinline__ void fft_filter_run_ct(C* s, int ld, const FftPlan& fwd, const FftPlan& inv, int tid,
+                                                  int nthr, Load& load, Mul& mul, Emit& emit) {
+  using P = CtPlan<L, E, false>;
+  constexpr int n = P::n;
+  constexpr int RF = P::rad(n - 1);
+  const C* tw = reinterpret_cast<const C*>(fwd.tw);
+  SmemRows<C> rows{s, ld};
+  if constexpr (n == 1) {
+    stage_filter<C, E, RF, L / RF>(L, fwd.st[0], tw, tid, nthr, load, mul, emit, false);
+  } else {
+    ct_stage<C, E, false, L, false, 0>(fwd, tw, tid, nthr, load, rows, false);
+    __syncthreads();
+    if constexpr (n > 2) { ct_stage<C, E, false, L, false, 1>(fwd, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 3) { ct_stage<C, E, false, L, false, 2>(fwd, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 4) { ct_stage<C, E, false, L, false, 3>(fwd, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    stage_filter<C, E, RF, L / RF>(L, stage_at(fwd, n - 1), tw, tid, nthr, rows, mul, rows, true);
+    __syncthreads();
+    if constexpr (n > 2) { ct_stage<C, E, true, L, true, 1>(inv, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 3) { ct_stage<C, E, true, L, true, 2>(inv, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 4) { ct_stage<C, E, true, L, true, 3>(inv, tw, tid, nthr, rows, rows, true); __syncthreads(); }
+    ct_stage<C, E, true, L, true, n - 1>(inv, tw, tid, nthr, rows, emit, false);
+  }
+}
+
+template <typename C, int E, int L, class Load, class Mul, class Emit>
+__device__ __forceinline__ bool fft_filter_run_fixed(C* s, int ld, const FftPlan& fwd, const FftPlan& inv, int tid,
+                                                     int nthr, Load& load, Mul& mul, Emit& emit) {
+  if constexpr (E == 16 && sizeof(C) == 8) {
+    if (ct_matches<L, E, false>(fwd) && ct_matches<L, E, true>(inv)) {
+      fft_filter_run_ct<C, E, L>(s, ld, fwd, inv, tid, nthr, load, mul, emit);
+      return true;
+    }
+  }
+  return false;
 }
 
 }  // namespace gad

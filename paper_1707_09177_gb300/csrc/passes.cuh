@@ -698,7 +698,8 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   xfwd_prologue<T, 2>(a, s, base, first, al, be, om, tid, nthr);
   __syncthreads();
   SmemRows<C> rows{s, a.ld};
-  fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
+  if (!fft_run_fixed<C, E, false, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true))
+    fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
   // split the packed half-length transform into the real-input spectrum
   const C* twx = reinterpret_cast<const C*>(a.twx);
   const int h1 = (M >> 1) + 1;
@@ -765,7 +766,8 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
     }
     __syncthreads();
     SmemRows<C> rows{s, a.ld};
-    fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
+    if (!fft_run_fixed<C, E, true, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true))
+      fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
     {
       // the epilogue's input vectors, fetched into L2 as whole tiles just
       // before the epilogue streams them: only its first round waits on DRAM.
@@ -871,7 +873,8 @@ __global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
     auto emit = [&](int w, int i, const C& x) {
       if (w < nvalid) S[(long long)w * L + i] = x;
     };
-    fft_filter_run<C, E>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit);
+    if (!fft_filter_run_fixed<C, E, 2048>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit))
+      fft_filter_run<C, E>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit);
     acc[0].s = p0;
     acc[1].s = p1;
     acc[2].s = p2;
