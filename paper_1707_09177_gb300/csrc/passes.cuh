@@ -698,7 +698,9 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   xfwd_prologue<T, 2>(a, s, base, first, al, be, om, tid, nthr);
   __syncthreads();
   SmemRows<C> rows{s, a.ld};
-  if (!fft_run_fixed<C, E, false, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true))
+  if (!fft_run_fixed<C, E, false, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true) &&
+      !fft_run_fixed<C, E, false, 256>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true) &&
+      !fft_run_fixed<C, E, false, 128>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true))
     fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
   // split the packed half-length transform into the real-input spectrum
   const C* twx = reinterpret_cast<const C*>(a.twx);
@@ -766,7 +768,9 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
     }
     __syncthreads();
     SmemRows<C> rows{s, a.ld};
-    if (!fft_run_fixed<C, E, true, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true))
+    if (!fft_run_fixed<C, E, true, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true) &&
+        !fft_run_fixed<C, E, true, 256>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true) &&
+        !fft_run_fixed<C, E, true, 128>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true))
       fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true);
     {
       // the epilogue's input vectors, fetched into L2 as whole tiles just
@@ -873,7 +877,9 @@ __global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
     auto emit = [&](int w, int i, const C& x) {
       if (w < nvalid) S[(long long)w * L + i] = x;
     };
-    if (!fft_filter_run_fixed<C, E, 2048>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit))
+    if (!fft_filter_run_fixed<C, E, 2048>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit) &&
+        !fft_filter_run_fixed<C, E, 512>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit) &&
+        !fft_filter_run_fixed<C, E, 256>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit))
       fft_filter_run<C, E>(s, a.ld, a.fft, a.fft_inv, tid, a.tfft, load, mul, emit);
     acc[0].s = p0;
     acc[1].s = p1;
@@ -900,7 +906,9 @@ __global__ void GAD_BOUNDS(T, E) k_yfwd(PassArgs<T> a) {
   const int kxn = a.kxn;
   auto load = [&](int w, int i) -> C { return S1[((long long)(z0 + w) * kxn + kx) * L + i]; };
   SmemRows<C> rows{s, a.ld};
-  fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true);
+  if (!fft_run_fixed<C, E, false, 512>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true) &&
+      !fft_run_fixed<C, E, false, 256>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true))
+    fft_run<C, E, false>(s, a.ld, a.fft, tid, a.tfft, load, rows, false, true);
   C* S2 = reinterpret_cast<C*>(a.S2) + (long long)f * a.SP + (long long)kx * L * a.nz + z0;
   store_transposed(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
 }
@@ -924,7 +932,9 @@ __global__ void GAD_BOUNDS(T, E) k_yinv(PassArgs<T> a) {
   const int kxn = a.kxn;
   auto emit = [&](int w, int i, const C& x) { S1[((long long)(z0 + w) * kxn + kx) * L + i] = x; };
   SmemRows<C> rows{s, a.ld};
-  fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false);
+  if (!fft_run_fixed<C, E, true, 512>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false) &&
+      !fft_run_fixed<C, E, true, 256>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false))
+    fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false);
 }
 
 // u += alpha p for fields whose last CG pass still owes it (Algorithm 3,
