@@ -137,6 +137,23 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
                         const void* u0, int* iterations, ad_status* status,
                         double* res_hist, double* true_res, void* stream);
 
+/* ad_deconvolve with the fields in HOST memory (Section 3, Eq. tau3; the same
+ * Algorithms 1-4 and stopping rules): copies u_bar to device buffers that the
+ * context owns for this grid and batch, solves from u0 = u_bar, and copies u*
+ * back, all on `stream`.
+ *   ubar        host, batch fields in the layout of ad_deconvolve (pinned
+ *               memory copies fastest; pageable memory works)
+ *   u_out       host, same size; may be ubar itself (u_bar is read in full
+ *               before u_out is written)
+ *   iterations, status, res_hist: as for ad_deconvolve
+ * Returns when u_out and the host outputs are ready, with ad_deconvolve's
+ * return value. Argument, allocation and CUDA errors (AD_ERR_ARG, AD_ERR_NOMEM,
+ * AD_ERR_CUDA) leave u_out untouched; per-field outcomes, AD_ERR_NONFINITE
+ * included, come with u_out written. */
+ad_status ad_deconvolve_host(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void* u_out,
+                             int batch, ad_method method, double tol, int maxit,
+                             int* iterations, ad_status* status, double* res_hist, void* stream);
+
 /* Solves G u = u_bar for `nfields` fields of possibly different grids (2D and
  * 3D, any supported sizes, dtypes and gammas) in one call: one CUDA graph
  * whose concurrent branches each solve the fields of one grid shape (gathered

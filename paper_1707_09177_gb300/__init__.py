@@ -45,7 +45,8 @@ AD_F32, AD_F64 = 0, 1
 EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvolve_batched", "ad_time_pass",
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
             "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
-            "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl", "ad_set_wait_limit")
+            "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl", "ad_set_wait_limit",
+            "ad_deconvolve_host")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec", 8: "sten"}
 
 
@@ -89,6 +90,9 @@ def load(path=None):
     lib.ad_deconvolve.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_i, c_d, c_i, c_p,
                                   c_p, c_p, c_p, c_p, c_p]
     lib.ad_deconvolve.restype = c_i
+    lib.ad_deconvolve_host.argtypes = [c_p, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_i, c_d, c_i, c_p, c_p, c_p,
+                                       c_p]
+    lib.ad_deconvolve_host.restype = c_i
     lib.ad_deconvolve_batched.argtypes = [c_p, c_i, ctypes.POINTER(ad_grid), c_p, c_p, c_i, c_d, c_i, c_p, c_p,
                                           c_p, c_p]
     lib.ad_deconvolve_batched.restype = c_i
@@ -165,7 +169,7 @@ def _check(st, ctx, per_field=False):
         raise GadError(st, "%s (%s)" % (lib.ad_status_str(st).decode(), lib.ad_last_error(ctx).decode()))
 
 
-def _grid(t, ndim, gamma):
+def _grid(t, ndim, gamma, host=False):
     import torch
     if t.dtype == torch.float32:
         dt = AD_F32
@@ -173,8 +177,8 @@ def _grid(t, ndim, gamma):
         dt = AD_F64
     else:
         raise TypeError("fields must be float32 or float64, got %s" % t.dtype)
-    if not t.is_cuda or not t.is_contiguous():
-        raise ValueError("fields must be contiguous CUDA tensors")
+    if t.is_cuda == host or not t.is_contiguous():
+        raise ValueError("fields must be contiguous %s tensors" % ("CPU" if host else "CUDA"))
     if ndim is None:
         if t.dim() == 2:
             ndim = 2
@@ -250,6 +254,32 @@ def deconvolve(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, u0=None, nd
                            ptr(its), ptr(sts), ptr(hist), ptr(tr), _stream_ptr(stream))
     _check(st, ctx, per_field=True)
     return Solve(u=out, iterations=its, status=sts, history=hist, true_residual=tr,
+                 launches=int(lib.ad_last_launch_count(ctx)))
+
+
+def deconvolve_host(ubar, gamma, method="bicgstab", tol=1e-6, maxit=1000, ndim=None, out=None, history=True,
+                    stream=None, space="physical", device=None):
+    """deconvolve() for fields in host memory: ``ubar`` is a contiguous CPU
+    tensor (pinned memory copies fastest); the library copies it to the GPU,
+    solves and copies u* back into ``out`` (a CPU tensor, may be ``ubar``)."""
+    import torch
+    lib = load()
+    ctx = context(device)
+    g, batch, _ = _grid(ubar, ndim, gamma, host=True)
+    code = method_code(method, space)
+    if out is None:
+        out = torch.empty_like(ubar)
+    if out.shape != ubar.shape or out.dtype != ubar.dtype or out.is_cuda or not out.is_contiguous():
+        raise ValueError("out must be a contiguous CPU tensor like u_bar")
+    its = np.zeros(batch, dtype=np.int32)
+    sts = np.zeros(batch, dtype=np.int32)
+    hist = np.full((batch, int(maxit) + 1), np.nan) if history else None
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else ctypes.c_void_p()
+    st = lib.ad_deconvolve_host(ctx, ctypes.byref(g), ctypes.c_void_p(ubar.data_ptr()),
+                                ctypes.c_void_p(out.data_ptr()), batch, code, float(tol), int(maxit), ptr(its),
+                                ptr(sts), ptr(hist), _stream_ptr(stream))
+    _check(st, ctx, per_field=True)
+    return Solve(u=out, iterations=its, status=sts, history=hist, true_residual=None,
                  launches=int(lib.ad_last_launch_count(ctx)))
 
 

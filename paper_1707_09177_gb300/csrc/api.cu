@@ -1738,6 +1738,32 @@ ad_status ad_deconvolve(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void
   return worst;
 }
 
+ad_status ad_deconvolve_host(ad_ctx* ctx, const ad_grid* grid, const void* ubar, void* u_out, int batch,
+                             ad_method method, double tol, int maxit, int* iterations, ad_status* status,
+                             double* res_hist, void* stream) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 0) return fail(ctx, AD_ERR_ARG, "batch < 0");
+  if (!method_ok(method)) return fail(ctx, AD_ERR_ARG, "unknown method");
+  if (maxit < 0 || !(tol >= 0.0) || !std::isfinite(tol)) return fail(ctx, AD_ERR_ARG, "need maxit >= 0 and finite tol >= 0");
+  if (batch == 0) { ctx->launches = 0; return AD_OK; }
+  if (!ubar || !u_out) return fail(ctx, AD_ERR_ARG, "NULL field pointer");
+  CK(cudaSetDevice(ctx->device));
+  Plan* p = nullptr;
+  if ((s = get_plan(ctx, grid, batch, &p)) != AD_OK || (s = ensure_io(ctx, p)) != AD_OK) return s;
+  const size_t bytes = (size_t)p->P * batch * (p->f64 ? 8 : 4);
+  cudaStream_t st = (cudaStream_t)stream;
+  // staged through the plan's own device buffers, so the solve's graph is the same on every call
+  CK(cudaMemcpyAsync(p->Bin, ubar, bytes, cudaMemcpyHostToDevice, st));
+  s = ad_deconvolve(ctx, grid, p->Bin, p->Bout, batch, method, tol, maxit, nullptr, iterations, status, res_hist,
+                    nullptr, stream);
+  if (s == AD_ERR_ARG || s == AD_ERR_CUDA || s == AD_ERR_NOMEM) return s;   // the solve did not run
+  CK(cudaMemcpyAsync(u_out, p->Bout, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
 // ---------------------------------------------------------------------------
 // Closure and statistics of deconvolved fields.
 
