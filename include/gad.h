@@ -100,10 +100,12 @@ typedef struct {
 typedef struct ad_ctx ad_ctx;   /* opaque: plans, twiddle tables, workspaces, graphs */
 
 /* Creates a context on CUDA device `device`. *ctx receives the handle, which
- * the caller releases with ad_destroy. */
+ * the caller releases with ad_destroy. Library housekeeping, no counterpart
+ * in the paper. */
 ad_status ad_create(ad_ctx** ctx, int device);
 
-/* Frees every device buffer, graph and stream the context owns. NULL is ignored. */
+/* Frees every device buffer, graph and stream the context owns. NULL is
+ * ignored. Library housekeeping, no counterpart in the paper. */
 void ad_destroy(ad_ctx* ctx);
 
 /* out = G in for `batch` fields (Section 4, Eq. df / Eq. df2, evaluated by
@@ -188,7 +190,8 @@ ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, 
  * All field and weight pointers are device pointers unless stated. */
 int64_t ad_guess_weight_count(void);
 
-/* Initial weights into a HOST array of n = ad_guess_weight_count() floats,
+/* Initial weights (learned guess; the stencil start restates the inverse of
+ * G, Eq. df) into a HOST array of n = ad_guess_weight_count() floats,
  * from a splitmix64 stream seeded by seed. stencil = 0: He-normal (last layer
  * scaled by 0.1). stencil != 0: the explicit local inverse of G,
  * u0 = u_bar - (delta/h)^2 L_h u_bar with the 7-point Laplacian L_h (channels
@@ -196,19 +199,22 @@ int64_t ad_guess_weight_count(void);
  * scaled by 1e-3, so training starts from that approximation. */
 ad_status ad_guess_init(float* weights_host, int64_t n, uint64_t seed, int stencil);
 
-/* u0 = u_bar + sigma * CNN(u_bar / sigma) for `batch` fields. */
+/* u0 = u_bar + sigma * A * CNN(u_bar / sigma) for `batch` fields (the learned
+ * guess described above; no counterpart in the paper). */
 ad_status ad_guess_infer(ad_ctx* ctx, const ad_grid* grid, const float* weights, const float* ubar, float* u0,
                          int batch, void* stream);
 
 /* Loss (host double, batch mean of ||u0 - u_true||^2 / ||u_true||^2) and its
- * gradient with respect to the weights (device float array) for one batch. */
+ * gradient with respect to the weights (device float array) for one batch
+ * (learned guess; no counterpart in the paper). */
 ad_status ad_guess_grad(ad_ctx* ctx, const ad_grid* grid, const float* weights, const float* ubar,
                         const float* utrue, int batch, float* grad, double* loss, void* stream);
 
 /* Trains the weights in place with Adam (lr, beta1 0.9, beta2 0.999) for
  * `epochs` passes over `npairs` (u_bar, u_true) pairs ([npairs][P] device
  * arrays) in minibatches of `batch` drawn by a seeded shuffle; loss_hist
- * (host double[epochs], may be NULL) receives each epoch's mean loss. */
+ * (host double[epochs], may be NULL) receives each epoch's mean loss.
+ * Learned guess; no counterpart in the paper. */
 ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const float* ubar, const float* utrue,
                          int epochs, int batch, double lr, uint64_t seed, float* weights, double* loss_hist,
                          void* stream);
@@ -320,7 +326,8 @@ ad_status ad_spectrum(ad_ctx* ctx, const ad_grid* grid, int nfields, int ncomp, 
 ad_status ad_histogram(ad_ctx* ctx, ad_dtype dtype, int64_t n, const void* x, double lo, double hi, int nbins,
                        int64_t* counts, void* stream);
 
-/* Vorticity by spectral differentiation (d/dx_d multiplies the Fourier
+/* Vorticity (the field whose PDFs Sections 4.1 and 4.2 compare) by spectral
+ * differentiation (d/dx_d multiplies the Fourier
  * coefficient by i k_d, zero at the Nyquist index), for nvel velocities:
  *   2D: u [nvel][2][Ny][Nx] -> omega [nvel][Ny][Nx], omega = dv/dx - du/dy
  *   3D: u [nvel][3][Nz][Ny][Nx] -> omega [nvel][3][...], omega = curl u
@@ -339,17 +346,21 @@ ad_status ad_set_wait_limit(ad_ctx* ctx, uint64_t ns);
 /* Enables (1, default) or disables (0) capture of each solve into one CUDA
  * graph whose iteration loop is a device-side conditional while node. With 0
  * the host launches the iteration body in chunks and polls the device
- * between chunks. Returns AD_ERR_ARG for a NULL context. */
+ * between chunks (the same iterations of Algorithms 1-4 either way). Returns
+ * AD_ERR_ARG for a NULL context. */
 ad_status ad_set_graph_mode(ad_ctx* ctx, int enable);
 
 /* Number of kernel launches the last ad_filter / ad_deconvolve call issued
- * (graph-internal launches counted per executed kernel node). */
+ * (graph-internal launches counted per executed kernel node). Library
+ * housekeeping, no counterpart in the paper. */
 int64_t ad_last_launch_count(const ad_ctx* ctx);
 
-/* Short English description of a status value (static storage). */
+/* Short English description of a status value (static storage). Library
+ * housekeeping, no counterpart in the paper. */
 const char* ad_status_str(ad_status s);
 
-/* Detail of the last error seen by the context (static per-context storage). */
+/* Detail of the last error seen by the context (static per-context storage).
+ * Library housekeeping, no counterpart in the paper. */
 const char* ad_last_error(const ad_ctx* ctx);
 
 #ifdef __cplusplus

@@ -34,6 +34,19 @@ def test_library_builds_and_exports_every_symbol():
     assert lib.ad_status_str(-2) == b"initial residual is not finite"
 
 
+def test_every_entry_point_states_its_source():
+    """Each declaration's comment cites the paper's passage it implements or
+    says that it has no counterpart there."""
+    with open(os.path.join(ROOT, "include", "gad.h")) as f:
+        src = f.read()
+    decl = re.compile(r"/\*((?:(?!\*/).)*)\*/\s*(?:const char\*|ad_status|void|int64_t)\s+(ad_[a-z_0-9]+)\(", re.S)
+    found = {m.group(2): m.group(1) for m in decl.finditer(src)}
+    assert sorted(found) == _declared()
+    for name, doc in found.items():
+        text = " ".join(re.sub(r"^\s*\*", "", line) for line in doc.splitlines())
+        assert re.search(r"Section|Eq\.|Algorithm|no\s+counterpart", text, re.I), name
+
+
 def test_binding_names_match_header():
     import paper_1707_09177_gb300 as gad
     assert sorted(gad.EXPORTED) == _declared()
