@@ -229,74 +229,88 @@ def _timed(fn):
     return r, time.perf_counter() - t0
 
 
-def _extra_workloads(gad, dev, extras):
-    """Other workloads of the method, one timed solve each after a warm-up:
-    the 3D velocity (256^3 x 3 components, gamma = 0.1, BiCGSTAB per
-    component to 1e-6) and the uneven batch (48 seeded sizes, 2D 256..4096
-    and 3D 64..384, gamma by grid size, BiCGSTAB to 1e-6 in one batched call,
-    against the same fields solved one shape group at a time)."""
+def _extra_workloads(gad, dev, extras, line):
+    """Other workloads of the method, one timed solve each after a warm-up,
+    each recorded in line["workloads"] as soon as it is measured (a failure is
+    recorded in line["errors"] and the next workload still runs): the 3D
+    velocity (256^3 x 3 components, gamma = 0.1, BiCGSTAB per component to
+    1e-6), the uneven batch (48 seeded sizes, 2D 256..4096 and 3D 64..384,
+    gamma by grid size, BiCGSTAB to 1e-6 in one batched call, against the same
+    fields solved one shape group at a time) and the 512^3 learned guess."""
     import torch
-    from synth import fields
-    out = {}
+    out = line["workloads"]
     if "3d256" in extras:
-        n = 256
-        v = fields.random_velocity_field((n, n, n), 0, fields.spectrum_3d_kolmogorov).astype(np.float32)
-        u_true = torch.from_numpy(v).to(dev)
-        ub = gad.filter(u_true, 0.1, ndim=3)
-        del u_true
-        r, t = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3))
-        its = [int(x) for x in r.iterations]
-        rs, ts = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3,
-                                               space="spectral"))
-        rp, tp = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3))
-        rq, tq = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3,
-                                               space="spectral"))
-        out["velocity3d_256_f32"] = {"mpoints_s": 3 * n ** 3 / t / 1e6, "ms": t * 1e3, "iterations": its,
-                                     "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches,
-                                     "spectral": {"mpoints_s": 3 * n ** 3 / ts / 1e6, "ms": ts * 1e3,
-                                                  "iterations": [int(x) for x in rs.iterations],
-                                                  "converged": bool(np.all(rs.status == gad.AD_OK))},
-                                     "pcg": {"mpoints_s": 3 * n ** 3 / tp / 1e6, "ms": tp * 1e3,
-                                             "iterations": [int(x) for x in rp.iterations],
-                                             "converged": bool(np.all(rp.status == gad.AD_OK))},
-                                     "pcg_spectral": {"mpoints_s": 3 * n ** 3 / tq / 1e6, "ms": tq * 1e3,
-                                                      "iterations": [int(x) for x in rq.iterations],
-                                                      "converged": bool(np.all(rq.status == gad.AD_OK))}}
-        if "closure" in extras:
-            out["closure_256"] = _closure_stats(gad, ub, r.u, n)
-        del ub, r, rp
+        _guarded(line, "velocity3d_256_f32", lambda: _velocity_256(gad, out, extras))
         torch.cuda.empty_cache()
     if "uneven48" in extras:
-        shapes = fields.uneven_batch(0)
-        ub, gammas = [], []
-        for i, sh in enumerate(shapes):
-            spec = _spectrum if len(sh) == 2 else fields.spectrum_3d_kolmogorov
-            g = fields.gamma_for_grid(sh)
-            ub.append(gad.filter(fields.random_scalar_field_torch(sh, 1000 + i, spec, device=dev), g, ndim=len(sh)))
-            gammas.append(g)
-        pts = float(sum(np.prod(sh) for sh in shapes))
-        res, t = _timed(lambda: gad.deconvolve_batched(ub, gammas, method="bicgstab", tol=1e-6, maxit=3000,
-                                                       history=False))
-        its = res[1]
-        launches = gad.last_launch_count()
-        # the same fields, one shape group per call
-        groups = {}
-        for i, sh in enumerate(shapes):
-            groups.setdefault(sh, []).append(i)
-
-        def seq():
-            for sh, idx in groups.items():
-                stacked = torch.stack([ub[i] for i in idx])
-                gad.deconvolve(stacked, gammas[idx[0]], method="bicgstab", tol=1e-6, maxit=3000, ndim=len(sh),
-                               history=False)
-        _, t_seq = _timed(seq)
-        out["uneven48_f32"] = {"mpoints_s": pts / t / 1e6, "ms": t * 1e3, "points": pts, "fields": len(shapes),
-                               "shape_groups": len(groups), "iterations_mean": float(np.mean(its)),
-                               "converged": bool(np.all(res[2] == gad.AD_OK)), "launches": launches,
-                               "one_call_per_group_mpoints_s": pts / t_seq / 1e6}
+        _guarded(line, "uneven48_f32", lambda: _uneven_48(gad, dev, out))
+        torch.cuda.empty_cache()
     if "learned512" in extras:
-        out["velocity3d_512_f32_learned"] = _learned_512(gad, dev)
-    return out
+        _guarded(line, "velocity3d_512_f32_learned",
+                 lambda: out.__setitem__("velocity3d_512_f32_learned", _learned_512(gad, dev)))
+        torch.cuda.empty_cache()
+
+
+def _velocity_256(gad, out, extras):
+    import torch
+    from synth import fields
+    n = 256
+    v = fields.random_velocity_field((n, n, n), 0, fields.spectrum_3d_kolmogorov).astype(np.float32)
+    u_true = torch.from_numpy(v).to(torch.device("cuda", torch.cuda.current_device()))
+    ub = gad.filter(u_true, 0.1, ndim=3)
+    del u_true
+    r, t = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3))
+    its = [int(x) for x in r.iterations]
+    rs, ts = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3,
+                                           space="spectral"))
+    rp, tp = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3))
+    rq, tq = _timed(lambda: gad.deconvolve(ub, 0.1, method="pcg", tol=1e-6, maxit=2000, ndim=3,
+                                           space="spectral"))
+    out["velocity3d_256_f32"] = {"mpoints_s": 3 * n ** 3 / t / 1e6, "ms": t * 1e3, "iterations": its,
+                                 "converged": bool(np.all(r.status == gad.AD_OK)), "launches": r.launches,
+                                 "spectral": {"mpoints_s": 3 * n ** 3 / ts / 1e6, "ms": ts * 1e3,
+                                              "iterations": [int(x) for x in rs.iterations],
+                                              "converged": bool(np.all(rs.status == gad.AD_OK))},
+                                 "pcg": {"mpoints_s": 3 * n ** 3 / tp / 1e6, "ms": tp * 1e3,
+                                         "iterations": [int(x) for x in rp.iterations],
+                                         "converged": bool(np.all(rp.status == gad.AD_OK))},
+                                 "pcg_spectral": {"mpoints_s": 3 * n ** 3 / tq / 1e6, "ms": tq * 1e3,
+                                                  "iterations": [int(x) for x in rq.iterations],
+                                                  "converged": bool(np.all(rq.status == gad.AD_OK))}}
+    if "closure" in extras:
+        out["closure_256"] = _closure_stats(gad, ub, r.u, n)
+
+
+def _uneven_48(gad, dev, out):
+    import torch
+    from synth import fields
+    shapes = fields.uneven_batch(0)
+    ub, gammas = [], []
+    for i, sh in enumerate(shapes):
+        spec = _spectrum if len(sh) == 2 else fields.spectrum_3d_kolmogorov
+        g = fields.gamma_for_grid(sh)
+        ub.append(gad.filter(fields.random_scalar_field_torch(sh, 1000 + i, spec, device=dev), g, ndim=len(sh)))
+        gammas.append(g)
+    pts = float(sum(np.prod(sh) for sh in shapes))
+    res, t = _timed(lambda: gad.deconvolve_batched(ub, gammas, method="bicgstab", tol=1e-6, maxit=3000,
+                                                   history=False))
+    its = res[1]
+    launches = gad.last_launch_count()
+    # the same fields, one shape group per call
+    groups = {}
+    for i, sh in enumerate(shapes):
+        groups.setdefault(sh, []).append(i)
+
+    def seq():
+        for sh, idx in groups.items():
+            stacked = torch.stack([ub[i] for i in idx])
+            gad.deconvolve(stacked, gammas[idx[0]], method="bicgstab", tol=1e-6, maxit=3000, ndim=len(sh),
+                           history=False)
+    _, t_seq = _timed(seq)
+    out["uneven48_f32"] = {"mpoints_s": pts / t / 1e6, "ms": t * 1e3, "points": pts, "fields": len(shapes),
+                           "shape_groups": len(groups), "iterations_mean": float(np.mean(its)),
+                           "converged": bool(np.all(res[2] == gad.AD_OK)), "launches": launches,
+                           "one_call_per_group_mpoints_s": pts / t_seq / 1e6}
 
 
 def _closure_stats(gad, ub, ustar, n):
@@ -468,9 +482,9 @@ def main():
     ap.add_argument("--space", default="physical", choices=["physical", "spectral"],
                     help="iteration space of the timed solve: physical (G by FFT passes every iteration, the "
                          "paper's formulation) or spectral (iterate on the half spectra, G pointwise)")
-    ap.add_argument("--extras", default="methods,3d256,closure,uneven48,learned512",
-                    help="comma list of extra measurements on rank 0: methods, 3d256, closure (needs 3d256), "
-                         "uneven48, learned512")
+    ap.add_argument("--extras", default="methods,3d512,3d256,closure,uneven48,learned512",
+                    help="comma list of extra measurements on rank 0: methods, 3d512 (pass rooflines of the "
+                         "512^3 x 3 velocity), 3d256, closure (needs 3d256), uneven48, learned512")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -562,83 +576,142 @@ def main():
                        "parallelism": "replicas" if ws > 1 else "1 gpu"},
             "iterations": {"min": min(iters), "max": max(iters), "mean": float(np.mean(iters))},
             "converged": ok, "e2e": e2e, "e2e_equals_device": e2e_same, "gpu_launches": int(launches), "clocks": clocks}
-
     extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
-    if rank == 0 and "methods" in extras:
-        # comparison methods on the same batch (one timed solve each)
-        methods = {}
-        for m, mi, sp in (("cg", 3000, "physical"), ("bicgstab", 3000, "physical"), ("pcg", 3000, "physical"),
-                          ("vancittert", VC_MAXIT, "physical"), ("cg", 3000, "spectral"), ("pcg", 3000, "spectral"),
-                          ("bicgstab", 3000, "spectral"), ("vancittert", VC_MAXIT, "spectral")):
-            step(m, maxit=mi, space=sp)
-            torch.cuda.synchronize()
-            ev0.record(stream)
-            r = step(m, maxit=mi, space=sp)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            t = ev0.elapsed_time(ev1)
-            its = [int(x) for x in r.iterations]
-            reached = bool(np.all(r.status == gad.AD_OK))
-            hfin = [float(r.history[b, its[b]]) for b in range(B)]
-            key = m if sp == "physical" else m + "_spectral"
-            methods[key] = {"ms": t, "iterations_mean": float(np.mean(its)), "reached_tol": reached,
-                            "mpoints_s": B * P / (t * 1e-3) / 1e6 if reached else None,
-                            "mpoints_s_per_pass": B * P * float(np.mean(its)) / (t * 1e-3) / 1e6,
-                            "h_final_max": max(hfin), "launches": r.launches}
-            if m == "vancittert":
-                methods[key]["maxit"] = VC_MAXIT
-        line["methods"] = methods
-
-    if rank == 0 and not args.no_extras:
-        # roofline of the dominant pass kernel, timed live with CUDA events
-        kxn = n[1] // 2 + 1
-        SP = kxn * n[0]
-        peak, src = _peaks()
-
-        def roofline(space):
-            passes = gad.time_passes(n, gamma, B, method=args.method, reps=20, space=space)
-            best = max(passes, key=lambda p: p["ms"])
-            total = sum(p["ms"] for p in passes)
-            for p in passes:
-                p["bytes"] = _pass_bytes(p["kind"], p["op"], P, SP, B, args.method)
-                p["gbs"] = p["bytes"] / (p["ms"] * 1e-3) / 1e9
-            return {"bound": "hbm", "kernel": "%s(op %d)" % (best["kind"], best["op"]),
-                    "achieved": best["gbs"], "peak": peak, "unit": "GB/s", "frac": best["gbs"] / peak,
-                    "peak_source": src + " hbm_gbs (copy, burst)",
-                    "traffic": _traffic(best["kind"], best["op"], space),
-                    "share_of_iteration": best["ms"] / total,
-                    "passes": [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in passes]}
-
-        line["roofline"] = roofline(args.space)
-        other = "spectral" if args.space == "physical" else "physical"
-        line["roofline_" + other] = roofline(other)
-        # the preconditioned CG pass set, with its stencil kernel
-        pp = gad.time_passes(n, gamma, B, method="pcg", reps=20)
-        for p in pp:
-            p["gbs"] = _pass_bytes(p["kind"], p["op"], P, SP, B, "pcg") / (p["ms"] * 1e-3) / 1e9
-        line["passes_pcg"] = [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in pp]
-
-        # the oracle on this host's cores, bounded sample
-        os.environ["OMP_NUM_THREADS"] = "1"
-        import oracle
-        ub0 = ubar_host[0].numpy().astype(np.float64)
-        sample_passes = 4
-        n0 = iters[0]
-        t_solve, per, t0 = _oracle_estimate(ub0, gamma, args.method, n0, sample_passes)
-        cpu_val = P / t_solve / 1e6
-        line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": ("oracle %s (float64 NumPy, 1 thread), field 0 of the batch: a 0-pass "
-                                           "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
-                                           "extrapolated to the %d passes the GPU solve of that field needed"
-                                           % (args.method, t0, sample_passes, per, n0))}
-    if rank == 0 and (extras & {"3d256", "closure", "uneven48", "learned512"}):
-        del out, dev_in, host_out
-        torch.cuda.empty_cache()
-        line["workloads"] = _extra_workloads(gad, dev, extras)
-    if rank == 0:
-        print(json.dumps(line))
+    try:
+        if rank == 0 and not args.no_extras:
+            _guarded(line, "roofline", lambda: _rooflines(gad, line, args, n, gamma, B))
+            _guarded(line, "cpu_baseline", lambda: _cpu_baseline(line, ubar_host, gamma, args.method, iters[0], P))
+        if rank == 0 and "methods" in extras:
+            _guarded(line, "methods", lambda: _methods(gad, line, step, stream, B, P))
+        if rank == 0 and "3d512" in extras:
+            _guarded(line, "roofline_3d512", lambda: _roofline_3d512(gad, line))
+        if rank == 0 and (extras & {"3d256", "closure", "uneven48", "learned512"}):
+            del out, host_out
+            torch.cuda.empty_cache()
+            line["workloads"] = {}
+            _extra_workloads(gad, dev, extras, line)
+    finally:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+def _guarded(line, name, fn):
+    """Runs one optional measurement; an exception is recorded in the line's
+    "errors" (and printed to stderr) instead of ending the benchmark."""
+    try:
+        fn()
+    except Exception as e:  # noqa: BLE001 - every failure of an extra is reported, none is fatal
+        import traceback
+        traceback.print_exc()
+        line.setdefault("errors", {})[name] = "%s: %s" % (type(e).__name__, str(e)[:400])
+
+
+def _pass_table(gad, shape, gamma, B, method, space, P, SP, reps=20):
+    passes = gad.time_passes(shape, gamma, B, method=method, reps=reps, space=space)
+    for p in passes:
+        p["bytes"] = _pass_bytes(p["kind"], p["op"], P, SP, B, method)
+        p["gbs"] = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+    return passes
+
+
+def _roofline_entry(passes, peak, src, space):
+    """The dominant pass kernel (longest per-launch time) against the HBM peak."""
+    best = max(passes, key=lambda p: p["ms"])
+    total = sum(p["ms"] for p in passes)
+    return {"bound": "hbm", "kernel": "%s(op %d)" % (best["kind"], best["op"]),
+            "achieved": best["gbs"], "peak": peak, "unit": "GB/s", "frac": best["gbs"] / peak,
+            "peak_source": src + " hbm_gbs (copy, burst)",
+            "traffic": _traffic(best["kind"], best["op"], space),
+            "share_of_iteration": best["ms"] / total,
+            "passes": [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in passes]}
+
+
+def _solve_entry(gad, passes, shape, gamma, B, method, space, peak, src, reps=10):
+    """One whole iteration body (every pass launch in order, CUDA events around
+    the sequence): its algorithmic bytes over its time, against the HBM peak."""
+    body_ms = gad.time_body(shape, gamma, B, method=method, reps=reps, space=space)
+    nbytes = float(sum(p["bytes"] for p in passes))
+    ach = nbytes / (body_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "peak_source": src + " hbm_gbs (copy, burst)", "bytes_per_body": nbytes, "ms_per_body": body_ms,
+            "launches_per_body": len(passes), "sum_of_pass_ms": float(sum(p["ms"] for p in passes))}
+
+
+def _rooflines(gad, line, args, n, gamma, B):
+    """Rooflines of the timed workload's passes, timed live with CUDA events:
+    the dominant kernel (`roofline`), the whole iteration body
+    (`roofline_solve`), the same for the other iteration space, and the
+    preconditioned CG pass set with its stencil kernel."""
+    P = n[0] * n[1]
+    SP = (n[1] // 2 + 1) * n[0]
+    peak, src = _peaks()
+    other = "spectral" if args.space == "physical" else "physical"
+    for space, key in ((args.space, ""), (other, "_" + other)):
+        passes = _pass_table(gad, n, gamma, B, args.method, space, P, SP)
+        line["roofline" + key] = _roofline_entry(passes, peak, src, space)
+        line["roofline_solve" + key] = _solve_entry(gad, passes, n, gamma, B, args.method, space, peak, src)
+    pp = _pass_table(gad, n, gamma, B, "pcg", "physical", P, SP)
+    line["passes_pcg"] = [{k: p[k] for k in ("index", "kind", "op", "ms", "gbs")} for p in pp]
+
+
+def _roofline_3d512(gad, line, method="bicgstab"):
+    """The 3D 512^3 x 3 velocity (gamma = 0.01): every pass of one BiCGSTAB
+    body and the whole body against the HBM peak, physical space."""
+    n = (512, 512, 512)
+    B, gamma = 3, 0.01
+    P = n[0] * n[1] * n[2]
+    SP = (n[2] // 2 + 1) * n[0] * n[1]
+    peak, src = _peaks()
+    passes = _pass_table(gad, n, gamma, B, method, "physical", P, SP, reps=5)
+    ent = _roofline_entry(passes, peak, src, "physical3d")
+    ent["solve"] = _solve_entry(gad, passes, n, gamma, B, method, "physical", peak, src, reps=5)
+    ent["workload"] = "velocity3d_512_f32 (3 components), %s body" % method
+    line["roofline_3d512"] = ent
+
+
+def _cpu_baseline(line, ubar_host, gamma, method, n0, P):
+    """The oracle on this host's cores (one thread), bounded sample: a 0-pass
+    and a 4-pass solve of field 0, extrapolated to the GPU's pass count."""
+    os.environ["OMP_NUM_THREADS"] = "1"
+    ub0 = ubar_host[0].numpy().astype(np.float64)
+    sample_passes = 4
+    t_solve, per, t0 = _oracle_estimate(ub0, gamma, method, n0, sample_passes)
+    cpu_val = P / t_solve / 1e6
+    line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": ("oracle %s (float64 NumPy, 1 thread), field 0 of the batch: a 0-pass "
+                                       "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
+                                       "extrapolated to the %d passes the GPU solve of that field needed"
+                                       % (method, t0, sample_passes, per, n0))}
+
+
+def _methods(gad, line, step, stream, B, P):
+    """Comparison methods on the same batch, one timed solve each."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    methods = {}
+    line["methods"] = methods
+    for m, mi, sp in (("cg", 3000, "physical"), ("bicgstab", 3000, "physical"), ("pcg", 3000, "physical"),
+                      ("vancittert", VC_MAXIT, "physical"), ("cg", 3000, "spectral"), ("pcg", 3000, "spectral"),
+                      ("bicgstab", 3000, "spectral"), ("vancittert", VC_MAXIT, "spectral")):
+        step(m, maxit=mi, space=sp)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        r = step(m, maxit=mi, space=sp)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1)
+        its = [int(x) for x in r.iterations]
+        reached = bool(np.all(r.status == gad.AD_OK))
+        hfin = [float(r.history[b, its[b]]) for b in range(B)]
+        key = m if sp == "physical" else m + "_spectral"
+        methods[key] = {"ms": t, "iterations_mean": float(np.mean(its)), "reached_tol": reached,
+                        "mpoints_s": B * P / (t * 1e-3) / 1e6 if reached else None,
+                        "mpoints_s_per_pass": B * P * float(np.mean(its)) / (t * 1e-3) / 1e6,
+                        "h_final_max": max(hfin), "launches": r.launches}
+        if m == "vancittert":
+            methods[key]["maxit"] = VC_MAXIT
 
 
 if __name__ == "__main__":

@@ -236,7 +236,9 @@ ad_status ad_autotune(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method met
  * buffers (caller memory is never touched) and with every field forced
  * active and no scalar update. `index` selects the launch within the
  * iteration body (0 .. count-1, in launch order); index = -1 only reports
- * the count. Outputs (host, may be NULL): ms_per_launch, kind (0 forward x,
+ * the count; index = -2 times the whole body (all its launches in order,
+ * ms_per_launch is then per body, kind and op are -1). Outputs (host, may
+ * be NULL): ms_per_launch, kind (0 forward x,
  * 1 inverse x, 2 filter, 3 forward y, 4 inverse y, 5 last-axis forward,
  * 6 last-axis inverse, 7 spectral-space pass, 8 preconditioner stencil), op (the fused
  * prologue/epilogue/dot code of that pass), count (launches per iteration).

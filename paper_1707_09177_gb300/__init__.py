@@ -312,6 +312,27 @@ def time_passes(shape, gamma, batch, method="bicgstab", dtype="f32", reps=20, st
     return out
 
 
+def time_body(shape, gamma, batch, method="bicgstab", dtype="f32", reps=10, stream=None, device=None,
+              space="physical"):
+    """Time (ms) of one whole iteration body of ``method`` (all its pass
+    launches in order), measured by the library with CUDA events in the
+    solve's launch shapes on its internal buffers."""
+    lib = load()
+    ctx = context(device)
+    g = ad_grid()
+    g.ndim = len(shape)
+    rev = list(reversed(shape)) + [1] * (3 - len(shape))
+    for i in range(3):
+        g.n[i] = int(rev[i])
+    g.dtype = AD_F32 if dtype == "f32" else AD_F64
+    g.gamma = float(gamma)
+    ms = ctypes.c_double()
+    st = lib.ad_time_pass(ctx, ctypes.byref(g), int(batch), method_code(method, space), -2, int(reps),
+                          _stream_ptr(stream), ctypes.byref(ms), None, None, None)
+    _check(st, ctx)
+    return float(ms.value)
+
+
 def deconvolve_batched(fields, gammas, method="bicgstab", tol=1e-6, maxit=1000, ndims=None, outs=None,
                        history=True, stream=None, space="physical"):
     """Solves G u = u_bar for a list of fields of uneven size in one library

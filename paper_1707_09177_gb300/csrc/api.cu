@@ -1357,15 +1357,20 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
   ctx->record = nullptr;
   if (s != AD_OK) return s;
   if (count) *count = (int)rec.size();
-  if (index < 0 || index >= (int)rec.size()) return index < 0 ? AD_OK : fail(ctx, AD_ERR_ARG, "pass index out of range");
-  LaunchRec r = rec[index];
+  if (index == -1) return AD_OK;
+  if (index < -2 || index >= (int)rec.size()) return fail(ctx, AD_ERR_ARG, "pass index out of range");
   // every field computes, no scalar update, no graph condition
-  r.af.force = r.ad.force = 1;
-  r.af.stage = r.ad.stage = SS_NONE;
-  r.af.set_cond = r.ad.set_cond = 0;
-  r.af.clear_cond = r.ad.clear_cond = 0;
-  if (kind) *kind = r.kind;
-  if (op) *op = r.f64 ? r.ad.op : r.af.op;
+  for (LaunchRec& q : rec) {
+    q.af.force = q.ad.force = 1;
+    q.af.stage = q.ad.stage = SS_NONE;
+    q.af.set_cond = q.ad.set_cond = 0;
+    q.af.clear_cond = q.ad.clear_cond = 0;
+  }
+  // index -2: the whole body, its launches in order
+  const size_t first = index == -2 ? 0 : (size_t)index, last = index == -2 ? rec.size() : (size_t)index + 1;
+  const LaunchRec& r = rec[first];
+  if (kind) *kind = index == -2 ? -1 : r.kind;
+  if (op) *op = index == -2 ? -1 : (r.f64 ? r.ad.op : r.af.op);
   cudaStream_t st = (cudaStream_t)stream;
   // a mid-solve state (pass 1, finite scalars), so that passes whose first
   // iteration skips work (p = r, no u update) are timed in their full form
@@ -1382,8 +1387,15 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
-  auto go = [&]() { return r.f64 ? launch_pass<double>(r.kind, r.E, r.grid, r.threads, r.smem, st, r.ad)
-                                  : launch_pass<float>(r.kind, r.E, r.grid, r.threads, r.smem, st, r.af); };
+  auto go = [&]() {
+    cudaError_t err = cudaSuccess;
+    for (size_t i = first; i < last && err == cudaSuccess; ++i) {
+      const LaunchRec& q = rec[i];
+      err = q.f64 ? launch_pass<double>(q.kind, q.E, q.grid, q.threads, q.smem, st, q.ad)
+                  : launch_pass<float>(q.kind, q.E, q.grid, q.threads, q.smem, st, q.af);
+    }
+    return err;
+  };
   cudaError_t e = go();                              // warm-up
   if (e == cudaSuccess) e = cudaEventRecord(e0, st);
   for (int i = 0; i < reps && e == cudaSuccess; ++i) e = go();
@@ -1395,7 +1407,7 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
   cudaEventDestroy(e1);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "ad_time_pass");
   if (ms_per_launch) *ms_per_launch = (double)ms / reps;
-  ctx->launches = reps + 1;
+  ctx->launches = (long long)(reps + 1) * (long long)(last - first);
   return AD_OK;
 }
 
