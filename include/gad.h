@@ -266,7 +266,9 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
  * stream are as for ad_filter; `in` and `out` may be the same buffer.
  *   The device address of the array is looked up (cudaGetSymbolAddress) by
  * the first call on each device, with that device current; make that first
- * call before any stream capture. All calls on a device share the array and
+ * call before any stream capture. The cached address is the device
+ * context's: after cudaDeviceReset on a device it is stale, and this entry
+ * point must not be called on that device again. All calls on a device share the array and
  * leave their contents in it (nothing in it needs clearing: every call
  * rewrites what it reads); calls whose work overlaps on the GPU (other
  * streams or host threads) race on it and must be serialized.

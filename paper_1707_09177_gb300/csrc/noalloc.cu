@@ -19,7 +19,10 @@
 // The array's name is only a host-side stand-in for the device object: its
 // device address is looked up with cudaGetSymbolAddress the first time the
 // entry point runs on a device (with that device current) and cached. That
-// first call per device should therefore come before any stream capture.
+// first call per device should therefore come before any stream capture. The
+// cached address belongs to the device's context: after cudaDeviceReset on a
+// device it is stale, so a process that resets a device must not call this
+// entry point on that device again.
 
 #include <cuda_runtime.h>
 
@@ -30,6 +33,7 @@
 #include "args.h"
 #include "fft.cuh"
 #include "launch.h"
+#include "plan.h"
 
 using namespace gad;
 
@@ -68,94 +72,21 @@ __global__ void k_static_twiddles(C* tw, int L) {
   tw[m] = C{(R)cs, (R)(-sn)};
 }
 
-int phys_s(int i) { return i + (i >> 4); }
-
-bool smooth23_s(long long n) {
-  if (n < 1) return false;
-  while (n % 2 == 0) n /= 2;
-  while (n % 3 == 0) n /= 3;
-  return n == 1;
-}
-
-int pow2_part_s(long long n) {
-  int p = 1;
-  while (n % 2 == 0 && p < (1 << 20)) { n /= 2; p *= 2; }
-  return p;
-}
-
-// Balanced radix list (at most 5 stages), fixed-size storage.
-bool radices_s(int L, int E, int* rad, int* nrad) {
-  int n = L, a = 0, b = 0, k = 0;
-  while (n % 2 == 0) { n /= 2; ++a; }
-  while (n % 3 == 0) { n /= 3; ++b; }
-  if (n != 1 || (b > 0 && E % 3 != 0)) return false;
-  const int maxlog = (E % 16 == 0) ? 4 : 3;
-  const int ns = a > 0 ? (a + maxlog - 1) / maxlog : 0;
-  if (b + ns > 5) return false;
-  for (int i = 0; i < b; ++i) rad[k++] = 3;
-  for (int i = 0; i < ns; ++i) rad[k++] = 1 << (a / ns + (i < a % ns ? 1 : 0));
-  for (int i = 0; i < k; ++i)
-    if (E % rad[i] != 0) return false;
-  *nrad = k;
-  return k > 0;
-}
-
-bool fft_s(int L, const int* rad, int nrad, const void* tab, long long Ltab, FftPlan& fp) {
-  fp = FftPlan{};
-  fp.L = L;
-  fp.nst = nrad;
-  fp.tw = tab;
-  long long ns = 1;
-  for (int q = 0; q < nrad; ++q) {
-    FftStage& s = fp.st[q];
-    s.radix = rad[q];
-    s.ns = (int)ns;
-    s.tw_step = (int)(Ltab / (ns * rad[q]));
-    s.rcp_lr = 1.0f / (float)(L / rad[q]);
-    s.rcp_ns = 1.0f / (float)ns;
-    ns *= rad[q];
-  }
-  return ns == L;
-}
-
 struct StaticPass {
-  int E = 0, W = 0, T = 0, ld = 0;
-  size_t smem = 0;
+  TileShape t;
   FftPlan fft{}, fft_inv{};
   float rcp_a = 0.f, rcp_b = 0.f;
   dim3 grid;
 };
 
+// The same plan and tile shape as the context-owning entry points build
+// (plan.h), so the pass kernels take the same code paths.
 bool plan_s(int L, int slots, int div, size_t cs, const void* tab, long long Ltab, bool with_inverse,
             StaticPass& pc) {
-  const int E = (L % 3 == 0) ? 24 : 16;
-  int rad[8], nrad = 0;
-  if (!radices_s(L, E, rad, &nrad) || !fft_s(L, rad, nrad, tab, Ltab, pc.fft)) return false;
-  if (with_inverse) {
-    int rev[8];
-    for (int i = 0; i < nrad; ++i) rev[i] = rad[nrad - 1 - i];
-    if (!fft_s(L, rev, nrad, tab, Ltab, pc.fft_inv)) return false;
-  }
-  int ld = phys_s(slots - 1) + 1;
-  if ((ld & 1) == 0) ++ld;
-  int bestW = 0, bestT = 0;
-  double best = 1e30;
-  for (int W = 1; W <= 4096; W *= 2) {
-    if (div > 0 && div % W != 0) break;
-    const long long tot = (long long)W * L;
-    if (tot % E != 0) continue;
-    const long long T = tot / E;
-    if (T < 1 || T > 256 || (size_t)W * ld * cs > 100 * 1024) continue;
-    const double score = std::fabs(std::log2((double)T / 256.0));
-    if (score < best - 1e-9) { best = score; bestW = W; bestT = (int)T; }
-  }
-  if (!bestW) return false;
-  pc.E = E;
-  pc.W = bestW;
-  pc.T = bestT;
-  pc.ld = ld;
-  pc.smem = (size_t)bestW * ld * cs;
-  return true;
+  const int E = pick_E(L);
+  if (!make_fft(L, E, tab, Ltab, pc.fft)) return false;
+  if (with_inverse && !make_fft(L, E, tab, Ltab, pc.fft_inv, true)) return false;
+  return choose_tile(L, E, slots, div, cs, pc.t);
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
@@ -185,15 +116,15 @@ ad_status run_static(const ad_grid* g, const void* in, void* out, int batch, cud
   StaticPass xf, fl, yf;
   const int Lf = g->ndim == 3 ? nz : ny;
   const int nseq = g->ndim == 3 ? kxn * ny : kxn;
-  bool ok = plan_s(M, M + 1, pow2_part_s(ny), cs, twx, nx, false, xf);
+  bool ok = plan_s(M, M + 1, pow2_part(ny), cs, twx, nx, false, xf);
   ok = ok && plan_s(Lf, Lf, 0, cs, g->ndim == 3 ? (const void*)twz : (const void*)twy, Lf, true, fl);
-  if (g->ndim == 3) ok = ok && plan_s(ny, ny, pow2_part_s(nz), cs, twy, ny, false, yf);
+  if (g->ndim == 3) ok = ok && plan_s(ny, ny, pow2_part(nz), cs, twy, ny, false, yf);
   if (!ok) return AD_ERR_ARG;
   xf.rcp_a = 1.0f / (float)(nx / 4);
   xf.rcp_b = 1.0f / (float)(M / 2 + 1);
-  xf.grid = dim3(ny * nz / xf.W, batch);
-  fl.grid = dim3((nseq + fl.W - 1) / fl.W, batch);
-  if (g->ndim == 3) yf.grid = dim3(kxn * (nz / yf.W), batch);
+  xf.grid = dim3(ny * nz / xf.t.W, batch);
+  fl.grid = dim3((nseq + fl.t.W - 1) / fl.t.W, batch);
+  if (g->ndim == 3) yf.grid = dim3(kxn * (nz / yf.t.W), batch);
 
   k_static_twiddles<C, T><<<(nx + 255) / 256, 256, 0, st>>>(twx, nx);
   k_static_twiddles<C, T><<<(ny + 255) / 256, 256, 0, st>>>(twy, ny);
@@ -213,9 +144,9 @@ ad_status run_static(const ad_grid* g, const void* in, void* out, int batch, cud
   a.S1 = S1; a.S2 = S2;
   a.batch = batch;
   auto launch = [&](int kind, const StaticPass& pc) {
-    a.W = pc.W; a.ld = pc.ld; a.fft = pc.fft; a.fft_inv = pc.fft_inv; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b;
-    a.tfft = pc.T;
-    return launch_pass<T>(kind, pc.E, pc.grid, (pc.T + 31) / 32 * 32, pc.smem, st, a);
+    a.W = pc.t.W; a.ld = pc.t.ld; a.fft = pc.fft; a.fft_inv = pc.fft_inv; a.rcp_a = pc.rcp_a; a.rcp_b = pc.rcp_b;
+    a.tfft = pc.t.T;
+    return launch_pass<T>(kind, pc.t.E, pc.grid, (pc.t.T + 31) / 32 * 32, pc.t.smem, st, a);
   };
   a.op = XF_COPY; a.A = static_cast<const T*>(in);
   if (launch(PK_XFWD, xf) != cudaSuccess) return AD_ERR_CUDA;
@@ -236,7 +167,7 @@ extern "C" ad_status ad_filter_static(const ad_grid* grid, const void* in, void*
     return AD_ERR_ARG;
   for (int d = 0; d < grid->ndim; ++d) {
     const long long n = grid->n[d];
-    if (n < 8 || n > 16384 || n % 2 != 0 || !smooth23_s(n)) return AD_ERR_ARG;
+    if (n < 8 || n > 16384 || n % 2 != 0 || !smooth23(n)) return AD_ERR_ARG;
   }
   if (grid->n[0] % 4 != 0) return AD_ERR_ARG;
   if (batch == 0) return AD_OK;
