@@ -25,26 +25,12 @@
 #include "args.h"
 #include "cnn.h"
 #include "launch.h"
+#include "plan.h"
 #include "state.h"
 
 using namespace gad;
 
 namespace {
-
-int phys_h(int i) { return i + (i >> 4); }
-
-bool smooth23(long long n) {
-  if (n < 1) return false;
-  while (n % 2 == 0) n /= 2;
-  while (n % 3 == 0) n /= 3;
-  return n == 1;
-}
-
-int pow2_part(long long n) {
-  int p = 1;
-  while (n % 2 == 0 && p < (1 << 20)) { n /= 2; p *= 2; }
-  return p;
-}
 
 struct PassCfg {
   int E = 0, W = 0, T = 0, ld = 0;
@@ -202,88 +188,17 @@ ad_status get_table(ad_ctx* ctx, long long L, bool f64, const void** out) {
   return AD_OK;
 }
 
-// Balanced radix list for a length L and per-thread element count E.
-bool radices_for(int L, int E, std::vector<int>& rad) {
-  rad.clear();
-  int n = L, a = 0, b = 0;
-  while (n % 2 == 0) { n /= 2; ++a; }
-  while (n % 3 == 0) { n /= 3; ++b; }
-  if (n != 1) return false;
-  if (b > 0 && E % 3 != 0) return false;
-  for (int i = 0; i < b; ++i) rad.push_back(3);
-  const int maxlog = (E % 16 == 0) ? 4 : 3;   // radix 16 for E = 16, 8 for E = 24
-  if (a > 0) {
-    const int ns = (a + maxlog - 1) / maxlog;
-    for (int i = 0; i < ns; ++i) {
-      const int e = a / ns + (i < a % ns ? 1 : 0);
-      rad.push_back(1 << e);
-    }
-  }
-  for (int r : rad) if (E % r != 0) return false;
-  return true;
-}
-
-bool make_fft_from(int L, const std::vector<int>& rad, const void* tab, long long Ltab, FftPlan& fp) {
-  if (rad.empty() || rad.size() > 5) return false;     // the kernels unroll at most 5 stages
-  fp = FftPlan{};
-  fp.L = L;
-  fp.nst = (int)rad.size();
-  fp.tw = tab;
-  long long ns = 1;
-  for (size_t q = 0; q < rad.size(); ++q) {
-    FftStage& s = fp.st[q];
-    s.radix = rad[q];
-    s.ns = (int)ns;
-    s.tw_step = (int)(Ltab / (ns * rad[q]));
-    s.rcp_lr = 1.0f / (float)(L / rad[q]);
-    s.rcp_ns = 1.0f / (float)ns;
-    ns *= rad[q];
-  }
-  return ns == L;
-}
-
-bool make_fft(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
-  std::vector<int> rad;
-  return radices_for(L, E, rad) && make_fft_from(L, rad, tab, Ltab, fp);
-}
-
-// The same radices in reverse order: the filter pass's inverse transform,
-// whose first stage meets the forward transform's last stage in registers.
-bool make_fft_reversed(int L, int E, const void* tab, long long Ltab, FftPlan& fp) {
-  std::vector<int> rad;
-  if (!radices_for(L, E, rad)) return false;
-  std::reverse(rad.begin(), rad.end());
-  return make_fft_from(L, rad, tab, Ltab, fp);
-}
-
-// Picks the tile width W (a power of two dividing `div`, or any power of two
-// when div = 0) and the block size T = W*L/E closest to 256 threads.
+// The tile shape of a pass (plan.h) copied into its launch configuration.
 bool choose_tile(int L, int E, int slots, int div, size_t csize, PassCfg& pc) {
-  int ld = phys_h(slots - 1) + 1;
-  if ((ld & 1) == 0) ++ld;
-  int bestW = 0, bestT = 0;
-  double bestScore = 1e30;
-  for (int W = 1; W <= 4096; W *= 2) {
-    if (div > 0 && div % W != 0) break;
-    const long long tot = (long long)W * L;
-    if (tot % E != 0) continue;
-    const long long T = tot / E;
-    if (T < 1 || T > 256) continue;
-    const size_t smem = (size_t)W * ld * csize;
-    if (smem > 100 * 1024) continue;
-    const double score = std::fabs(std::log2((double)T / 256.0));
-    if (score < bestScore - 1e-9) { bestScore = score; bestW = W; bestT = (int)T; }
-  }
-  if (!bestW) return false;
-  pc.E = E;
-  pc.W = bestW;
-  pc.T = bestT;
-  pc.ld = ld;
-  pc.smem = (size_t)bestW * ld * csize;
+  TileShape ts;
+  if (!gad::choose_tile(L, E, slots, div, csize, ts)) return false;
+  pc.E = ts.E;
+  pc.W = ts.W;
+  pc.T = ts.T;
+  pc.ld = ts.ld;
+  pc.smem = ts.smem;
   return true;
 }
-
-int pick_E(int L) { return (L % 3 == 0) ? 24 : 16; }
 
 // A method value: one of AD_VANCITTERT .. AD_SD, optionally OR-ed with AD_SPECTRAL.
 bool method_ok(int m) {
@@ -368,7 +283,7 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
   const int nseq = p->ndim == 3 ? p->kxn * p->ny : p->kxn;
   ok = ok && choose_tile(Lf, pick_E(Lf), Lf, 0, cs, p->fl);
   ok = ok && make_fft(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft);
-  ok = ok && make_fft_reversed(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft_inv);
+  ok = ok && make_fft(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft_inv, true);
   p->fl.rcp_a = 1.0f / (float)(Lf / 2);
   p->fl.rcp_b = 1.0f / (float)Lf;
   p->fl.grid = dim3((nseq + std::max(p->fl.W, 1) - 1) / std::max(p->fl.W, 1), batch);
@@ -965,8 +880,7 @@ struct TileSlot {
 };
 
 void set_tile(const Plan* p, PassCfg& pc, int kind, int L, int slots, int W) {
-  int ld = phys_h(slots - 1) + 1;
-  if ((ld & 1) == 0) ++ld;
+  const int ld = tile_ld(slots);
   pc.W = W;
   pc.T = (int)((long long)W * L / pc.E);
   pc.ld = ld;
@@ -1067,8 +981,7 @@ ad_status autotune_plan(ad_ctx* ctx, Plan* p, int method, int reps) {
       const long long tot = (long long)W * sl.L;
       if (tot % sl.pc->E != 0) continue;
       const long long T = tot / sl.pc->E;
-      int ld = phys_h(sl.slots - 1) + 1;
-      if ((ld & 1) == 0) ++ld;
+      const int ld = tile_ld(sl.slots);
       if (T < 32 || T > 256 || (size_t)W * ld * cs > 100 * 1024) continue;
       PassCfg trial = *sl.pc;
       set_tile(p, trial, sl.kind, sl.L, sl.slots, W);
@@ -1134,9 +1047,20 @@ ad_status get_cnn(ad_ctx* ctx, const ad_grid* g, int B, bool training, CnnWork**
         (s = cnn_alloc(ctx, cw, (void**)&w.H1, act)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.H2, act)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.H3, act)) != AD_OK ||
-        (s = cnn_alloc(ctx, cw, (void**)&w.sumsq, sizeof(double) * (2 * B + 1))) != AD_OK)
+        (s = cnn_alloc(ctx, cw, (void**)&w.sumsq, sizeof(double) * (2 * B + 1))) != AD_OK ||
+        (s = cnn_alloc(ctx, cw, (void**)&w.flag, sizeof(int))) != AD_OK)
       return s;
+    if (cudaMemset(w.flag, 0, sizeof(int)) != cudaSuccess) return cuda_fail(ctx, cudaGetLastError(), "cnn flag");
+    if (gad::conv_tc_shape_ok((int)g->n[0], (int)g->n[1], (int)g->n[2])) {
+      const size_t ib = gad::conv_tc_image_bytes();
+      if ((s = cnn_alloc(ctx, cw, (void**)&w.umma2, ib)) != AD_OK ||
+          (s = cnn_alloc(ctx, cw, (void**)&w.umma3, ib)) != AD_OK ||
+          (s = cnn_alloc(ctx, cw, (void**)&w.umma2t, ib)) != AD_OK ||
+          (s = cnn_alloc(ctx, cw, (void**)&w.umma3t, ib)) != AD_OK)
+        return s;
+    }
   }
+  w.wait_ns = ctx->wait_ns;
   if (training && !w.grad) {
     if ((s = cnn_alloc(ctx, cw, (void**)&w.grad, sizeof(float) * kCnnWeights)) != AD_OK ||
         (s = cnn_alloc(ctx, cw, (void**)&w.m, sizeof(float) * kCnnWeights)) != AD_OK ||
@@ -1151,6 +1075,20 @@ ad_status get_cnn(ad_ctx* ctx, const ad_grid* g, int B, bool training, CnnWork**
       return s;
   }
   *out = cw;
+  return AD_OK;
+}
+
+// Reads back (and clears) the flag the tensor-core convolution sets when one
+// of its bounded waits gave up; waits for the stream. AD_ERR_TIMEOUT if set.
+ad_status cnn_flag_status(ad_ctx* ctx, CnnWork* cw, cudaStream_t st) {
+  int h = 0;
+  CK(cudaMemcpyAsync(&h, cw->w.flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (h) {
+    CK(cudaMemsetAsync(cw->w.flag, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    return fail(ctx, AD_ERR_TIMEOUT, "a bounded wait of the tensor-core convolution gave up");
+  }
   return AD_OK;
 }
 
@@ -1570,7 +1508,9 @@ ad_status ad_guess_infer(ad_ctx* ctx, const ad_grid* grid, const float* weights,
   CK(cnn_pack(cw->w, st));
   CK(cnn_forward(cw->w, ubar, u0, nullptr, (int)grid->n[0], (int)grid->n[1], (int)grid->n[2], batch,
                  cnn_ascale(grid->gamma), st));
-  ctx->launches = 5 + 5 + 1;
+  ctx->launches = 5 + 5 + 1 + (cw->w.umma2 ? 4 : 0);
+  // the tensor-core path reports a bounded wait that gave up
+  if (cw->w.umma2) return cnn_flag_status(ctx, cw, st);
   return AD_OK;
 }
 
@@ -1594,7 +1534,7 @@ ad_status ad_guess_grad(ad_ctx* ctx, const ad_grid* grid, const float* weights, 
   CK(cudaMemcpyAsync(&l, cw->w.sumsq + 2 * batch, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (loss) *loss = l;
-  return AD_OK;
+  return cnn_flag_status(ctx, cw, st);
 }
 
 ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const float* ubar, const float* utrue,
@@ -1654,7 +1594,7 @@ ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const flo
   CK(cudaMemcpyAsync(weights, cw->w.master, sizeof(float) * kCnnWeights, cudaMemcpyDeviceToDevice, st));
   CK(cudaStreamSynchronize(st));
   ctx->launches = launches;
-  return AD_OK;
+  return cnn_flag_status(ctx, cw, st);
 }
 
 ad_status ad_set_graph_mode(ad_ctx* c, int enable) {

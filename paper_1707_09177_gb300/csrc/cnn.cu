@@ -708,8 +708,14 @@ cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const
     if (e != cudaSuccess) return e;
   }
   const dim3 gc((unsigned)(X / TX) * Y * Z, B);
-  k_conv_mma<<<gc, TX, sm, s>>>(w.H1, w.frag2, w.H2, nullptr, X, Y, Z, TX, 0);
-  k_conv_mma<<<gc, TX, sm, s>>>(w.H2, w.frag3, w.H3, nullptr, X, Y, Z, TX, 0);
+  if (w.umma2 && conv_tc_shape_ok(X, Y, Z)) {
+    if ((e = conv_tc_forward(w.H1, w.umma2, w.H2, nullptr, X, Y, Z, B, 0, w.flag, w.wait_ns, s)) != cudaSuccess ||
+        (e = conv_tc_forward(w.H2, w.umma3, w.H3, nullptr, X, Y, Z, B, 0, w.flag, w.wait_ns, s)) != cudaSuccess)
+      return e;
+  } else {
+    k_conv_mma<<<gc, TX, sm, s>>>(w.H1, w.frag2, w.H2, nullptr, X, Y, Z, TX, 0);
+    k_conv_mma<<<gc, TX, sm, s>>>(w.H2, w.frag3, w.H3, nullptr, X, Y, Z, TX, 0);
+  }
   if (sm > 48 * 1024) {
     e = cudaFuncSetAttribute(k_conv_out_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -726,6 +732,14 @@ cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s) {
   k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW2, w.frag2t, 1);
   k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW3, w.frag3t, 1);
   k_pack_frag4<<<(TAPS * 2 * 32 + 255) / 256, 256, 0, s>>>(w.master + kW4, w.frag4);
+  if (w.umma2) {
+    cudaError_t e;
+    if ((e = conv_tc_pack(w.master + kW2, w.umma2, 0, s)) != cudaSuccess ||
+        (e = conv_tc_pack(w.master + kW3, w.umma3, 0, s)) != cudaSuccess ||
+        (e = conv_tc_pack(w.master + kW2, w.umma2t, 1, s)) != cudaSuccess ||
+        (e = conv_tc_pack(w.master + kW3, w.umma3t, 1, s)) != cudaSuccess)
+      return e;
+  }
   return cudaGetLastError();
 }
 
@@ -760,11 +774,20 @@ cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, i
   if (e != cudaSuccess) return e;
   k_wgrad_mma<<<kWgradBlocks, 288, smw, s>>>(w.H2, w.dA, w.part, X, Y, Z, B, TX);
   k_reduce_parts<<<(TAPS * C * C + 255) / 256, 256, 0, s>>>(w.part, kWgradBlocks, TAPS * C * C, w.grad + kW3);
-  k_conv_mma<<<gc, TX, sm, s>>>(w.dA, w.frag3t, w.dB, w.H2, X, Y, Z, TX, 1);
+  const bool tc = w.umma2 && conv_tc_shape_ok(X, Y, Z);
+  if (tc) {
+    if ((e = conv_tc_forward(w.dA, w.umma3t, w.dB, w.H2, X, Y, Z, B, 1, w.flag, w.wait_ns, s)) != cudaSuccess) return e;
+  } else {
+    k_conv_mma<<<gc, TX, sm, s>>>(w.dA, w.frag3t, w.dB, w.H2, X, Y, Z, TX, 1);
+  }
   // layer 2: dW2 from (H1, dZ2); dZ1 = conv^T(dZ2, W2) masked by H1
   k_wgrad_mma<<<kWgradBlocks, 288, smw, s>>>(w.H1, w.dB, w.part, X, Y, Z, B, TX);
   k_reduce_parts<<<(TAPS * C * C + 255) / 256, 256, 0, s>>>(w.part, kWgradBlocks, TAPS * C * C, w.grad + kW2);
-  k_conv_mma<<<gc, TX, sm, s>>>(w.dB, w.frag2t, w.dA, w.H1, X, Y, Z, TX, 1);
+  if (tc) {
+    if ((e = conv_tc_forward(w.dB, w.umma2t, w.dA, w.H1, X, Y, Z, B, 1, w.flag, w.wait_ns, s)) != cudaSuccess) return e;
+  } else {
+    k_conv_mma<<<gc, TX, sm, s>>>(w.dB, w.frag2t, w.dA, w.H1, X, Y, Z, TX, 1);
+  }
   // layer 1
   k_wgrad_1ch<<<kSmallBlocks, 256, sm1, s>>>(ubar, w.sumsq, w.dA, w.part, X, Y, Z, B, TW, 0);
   k_reduce_parts<<<(TAPS * C + 255) / 256, 256, 0, s>>>(w.part, kSmallBlocks, TAPS * C, w.grad + kW1);

@@ -35,6 +35,12 @@ struct CnnBuffers {
   float* g = nullptr;          // dL/dy of the last layer [B][P]
   double* sumsq = nullptr;     // [B] sum u_bar^2, [B] sum u_true^2, [1] loss
   float* part = nullptr;       // weight-gradient partials
+  __nv_bfloat16* umma2 = nullptr;   // layer 2/3 weights as tcgen05 B operands in shared-memory order (forward)
+  __nv_bfloat16* umma3 = nullptr;
+  __nv_bfloat16* umma2t = nullptr;  // flipped, channel-swapped (backward data)
+  __nv_bfloat16* umma3t = nullptr;
+  int* flag = nullptr;              // set to 1 by a tensor-core kernel whose bounded wait ran out
+  unsigned long long wait_ns = 1000000000ull;   // limit of those waits
 };
 
 // floats of the weight-gradient partial buffer
@@ -49,5 +55,15 @@ cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const
                         int B, double ascale, cudaStream_t s);
 cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, int Z, int B, cudaStream_t s);
 cudaError_t cnn_adam(const CnnBuffers& w, int step, float lr, cudaStream_t s);
+
+// 32 -> 32 layers on the tcgen05 tensor cores (conv_tc.cu): grids whose x side
+// is a multiple of 128; others use the warp-level kernels of cnn.cu.
+bool conv_tc_shape_ok(int X, int Y, int Z);
+size_t conv_tc_image_bytes();
+cudaError_t conv_tc_pack(const float* W, __nv_bfloat16* img, int transposed, cudaStream_t s);
+// Hout = epilogue(conv(Hin, W)); mode 0: ReLU, mode 1: zero where Hmask <= 0
+cudaError_t conv_tc_forward(const __nv_bfloat16* Hin, const __nv_bfloat16* Wimg, __nv_bfloat16* Hout,
+                            const __nv_bfloat16* Hmask, int X, int Y, int Z, int B, int mode, int* flag,
+                            unsigned long long wait_ns, cudaStream_t s);
 
 }  // namespace gad
