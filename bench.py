@@ -585,6 +585,8 @@ def main():
             _guarded(line, "methods", lambda: _methods(gad, line, step, stream, B, P))
         if rank == 0 and "3d512" in extras:
             _guarded(line, "roofline_3d512", lambda: _roofline_3d512(gad, line))
+        if rank == 0 and "learned512" in extras:
+            _guarded(line, "roofline_conv", lambda: _roofline_conv(gad, line))
         if rank == 0 and (extras & {"3d256", "closure", "uneven48", "learned512"}):
             del out, host_out
             torch.cuda.empty_cache()
@@ -669,6 +671,30 @@ def _roofline_3d512(gad, line, method="bicgstab"):
     ent["solve"] = _solve_entry(gad, passes, n, gamma, B, method, "physical", peak, src, reps=5)
     ent["workload"] = "velocity3d_512_f32 (3 components), %s body" % method
     line["roofline_3d512"] = ent
+
+
+def _roofline_conv(gad, line):
+    """One 32 -> 32 layer of the learned guess's network on the 512^3 x 3
+    velocity (the inference launch shape), timed by the library with CUDA
+    events, against the measured bf16 tensor peak (burst: the kernel is timed
+    alone): 55,296 flop per grid point (27 taps x 32 x 32 multiply-adds)."""
+    n, B = 512, 3
+    ms, tc = gad.guess_time_conv((n, n, n), B, reps=5)
+    flops = B * n ** 3 * 27 * 32 * 32 * 2.0
+    peak, src = _bf16_peak()
+    ach = flops / (ms * 1e-3) / 1e12
+    line["roofline_conv"] = {"bound": "tensor", "kernel": "k_conv_tc" if tc else "k_conv_mma", "achieved": ach,
+                             "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "ms": ms,
+                             "peak_source": src + " bf16_tflops (cuBLAS, burst)", "traffic": None,
+                             "workload": "velocity3d_512_f32 learned guess, one 32->32 layer, 3 components"}
+
+
+def _bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    return 1900.0, "fallback"
 
 
 def _cpu_baseline(line, ubar_host, gamma, method, n0, P):

@@ -2,22 +2,41 @@
 // tensor cores (tcgen05): an implicit GEMM whose accumulator lives in tensor
 // memory and whose activation rows are staged by TMA.
 //
-// One CTA owns an x-segment of 128 points of one (field, z) plane and marches
-// along y. Output row y is the GEMM
-//     D[128 points][32 out channels] = sum over 27 taps, 2 halves of 16 input channels
-//         A_tap[128][16] * B_tap[16][32],
-// 54 tcgen05.mma (M = 128, N = 32, K = 16, bf16 inputs, float32 accumulation in
-// tensor memory). A_tap is not materialised: the staged rows hold every point
-// of the segment plus one periodic neighbour on each side, 16 bytes (8
-// channels) per point and channel group, in the no-swizzle K-major core-matrix
-// layout with consecutive points 16 bytes apart; the x offset of a tap is a
-// shift of the descriptor's start address by 16 bytes, the y and z offsets
-// select the staged row. Rows are staged once per CTA in a ring of five y
-// positions x three z planes (TMA for the 128 interior points of each channel
-// group, plain loads for the two periodic neighbours), two y steps ahead of the
-// tensor cores. The accumulator is double-buffered in tensor memory: the MMAs
-// of row y run while the four warps read row y - 1 back (tcgen05.ld), apply
-// the epilogue (ReLU, or the ReLU mask of the backward pass) and store bf16.
+// One CTA owns an x-segment of 128 points of one (field, z) plane and a range
+// of y. Output row y is
+//     D_y[128 points][32 out channels] = sum over taps (dz, dy, dx) and 2 halves of
+//         16 input channels of  A_{z+dz-1, y+dy-1, dx}[128][16] * W_{dz,dy,dx}[16][32].
+// The CTA walks the INPUT rows y' instead: one input row (three z planes)
+// contributes to the three output rows y'+1, y', y'-1 through the taps
+// dy = 0, 1, 2, so for each (dz, dx, K half) one tcgen05.mma with N = 96
+// (M = 128 points, K = 16 channels, bf16 inputs, float32 accumulation) adds
+// A_{dz, y', dx} times the three tap blocks [W_{dz,0,dx} | W_{dz,1,dx} |
+// W_{dz,2,dx}] into the accumulators of those three output rows at once: 18
+// MMAs per input row instead of 54 with N = 32, and every staged row is used
+// by one batch of MMAs. The accumulators of the output rows live in a ring of
+// sixteen 32-column slots of tensor memory laid out so that rows y'+1, y',
+// y'-1 occupy consecutive slots (slot(y) decreases with y); where the three
+// wrap around the ring the MMA is split in two. Every slot starts at zero (the
+// epilogue clears a slot after reading it) and every MMA accumulates.
+// A_{dz, y', dx} is not materialised: the staged rows hold every point of the
+// segment plus one periodic neighbour on each side, 16 bytes (8 channels) per
+// point and channel group, in the no-swizzle K-major core-matrix layout with
+// consecutive points 16 bytes apart, so the x offset of a tap is a shift of
+// the descriptor's start address by 16 bytes. The warps have one role each
+// and hand work over through mbarriers:
+//   warp 4 (producer): stages input rows (three z planes x four channel
+//     groups: TMA for the 128 interior points, plain loads for the two periodic
+//     neighbours) into a ring of five slots, refilling a slot as soon as the
+//     MMAs of the row it held have completed;
+//   warp 5 (MMA): allocates the tensor memory, and for each input row waits
+//     for its staging (and for the slot of the output row entering the ring to
+//     be cleared), issues its MMAs, and commits them to the "empty" barrier of
+//     the input slot and to the "full" barrier of the output row y'-1, which
+//     no later input row touches;
+//   warps 0-3 (epilogue): wait for an output row, read its accumulator back
+//     (tcgen05.ld, warp w owning tensor-memory lanes 32w .. 32w+31), clear it
+//     (tcgen05.st of zeros), release the slot, apply the epilogue (ReLU, or the
+//     ReLU mask of the backward pass) and store bf16.
 //
 // Every mbarrier wait is bounded by %globaltimer; a CTA whose wait runs out
 // sets the error flag, stops issuing work, waits (bounded) for what it has in
@@ -45,16 +64,19 @@ constexpr int kPlane = kPlaneEntries * 16;     // 2304 bytes
 constexpr int kInterior = 8;                   // entry of the segment's first point (128-byte aligned)
 constexpr int kRow = 4 * kPlane;               // one staged row: 4 channel groups
 constexpr int kSlots = 5;                      // y positions in the ring
-constexpr int kWBytes = kTaps * 2 * 1024;      // B operands: per tap and K half, 32 x 16 bf16
+constexpr int kBBlock = 96 * 16 * 2;            // B operand of one (dz, dx, K half): 96 x 16 bf16
+constexpr int kWBytes = 9 * 2 * kBBlock;          // all of them (55296 bytes)
 constexpr int kRowsOff = kWBytes;              // staged rows after the weights
 constexpr int kBarOff = kRowsOff + kSlots * 3 * kRow;
-constexpr int kSmemUsed = kBarOff + 128;
+constexpr int kSmemUsed = kBarOff + 512;
 // the whole shared memory of an SM (one CTA per SM): every address a
 // descriptor can reach under either reading of its two stride fields stays
 // inside the allocation
 constexpr int kSmemAlloc = 227 * 1024;
 constexpr int kTxBytes = 3 * 4 * kTM * 16;     // bytes of one ring fill (3 rows x 4 groups x 128 points)
-constexpr uint32_t kTmemCols = 64;             // two 32-column accumulators
+constexpr int kAcc = 16;                       // output-row accumulators in tensor memory
+constexpr uint32_t kTmemCols = 32 * kAcc;      // 32 float32 columns each: all 512 columns
+constexpr int kThreads = 192;                  // 4 epilogue warps, producer warp, MMA warp
 
 static_assert(kSmemUsed <= kSmemAlloc, "shared-memory layout exceeds the allocation");
 static_assert(kPlane % 128 == 0 && kRow % 1024 == 0 && kRowsOff % 1024 == 0, "TMA destinations 128-byte aligned");
@@ -93,16 +115,17 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
 }
 
 // Instruction descriptor of tcgen05.mma kind::f16: D float32, A and B bf16,
-// both K-major, N = 32, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(32 >> 3) << 17) |
-                            ((uint32_t)(kTM >> 4) << 24);
+// both K-major, M = 128, N given (a multiple of 16, at most 256).
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, uint32_t idesc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
+      "setp.ne.b32 p, 1, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-      ::"r"(dtmem), "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      ::"r"(dtmem), "l"(a), "l"(b), "r"(idesc)
       : "memory");
 }
 
@@ -134,11 +157,11 @@ struct ConvTcArgs {
   int* flag;                     // set to 1 when a bounded wait runs out
 };
 
-// grid x = (X/128) * Z * (Y/ychunk), grid y = fields; 128 threads
-__global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvTcArgs a) {
+// grid x = (X/128) * Z * (Y/ychunk), grid y = fields; kThreads threads
+__global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__ CUtensorMap tmap, const ConvTcArgs a) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nxs = a.X / kTM, nyc = a.Y / a.ychunk;
+  const int nxs = a.X / kTM;
   int r = blockIdx.x;
   const int xs = r % nxs;
   r /= nxs;
@@ -146,12 +169,19 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
   const int yc = r / a.Z;
   const int b = blockIdx.y;
   const int x0 = xs * kTM, yb = yc * a.ychunk, ny = a.ychunk;
-  (void)nyc;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOff);        // [0..4] ring fills, [5..6] MMA done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kBarOff + 64);
+  // barriers: full[5] / empty[5] (input ring slot staged / read by its MMAs),
+  // accf[16] (output row's accumulator complete), acce[16] (read back and cleared)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOff);
+  const uint32_t full0 = su32(bars), empty0 = full0 + 8 * kSlots, accf0 = empty0 + 8 * kSlots,
+                 acce0 = accf0 + 8 * kAcc;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kBarOff + 8 * (2 * kSlots + 2 * kAcc));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* rows_issued = reinterpret_cast<int*>(tmem_slot + 2);     // producer: input rows staged or in flight
+  int* rows_done = reinterpret_cast<int*>(tmem_slot + 3);       // MMA warp: input rows whose MMAs it committed
+  int* rows_ready = reinterpret_cast<int*>(tmem_slot + 4);      // MMA warp: input rows whose staging it waited for
   const uint32_t sbase = su32(sm);
 
-  if (warp == 0) {
+  if (warp == 5) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
                  "r"(kTmemCols)
                  : "memory");
@@ -159,186 +189,255 @@ __global__ void __launch_bounds__(128, 1) k_conv_tc(const __grid_constant__ CUte
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
   if (tid == 0) {
-    for (int i = 0; i < kSlots + 2; ++i)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bars[i])) : "memory");
+    for (int i = 0; i < kSlots; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(full0 + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(empty0 + 8 * i) : "memory");
+    }
+    for (int i = 0; i < kAcc; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(accf0 + 8 * i) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(acce0 + 8 * i) : "memory");
+    }
+    *abort_flag = 0;
+    *rows_issued = 0;
+    *rows_done = 0;
+    *rows_ready = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  // weights: generic copy of the B-operand image
+  // weights: generic copy of the B-operand image, visible to the tensor cores
   {
     uint4* w = reinterpret_cast<uint4*>(sm);
-    for (int i = tid; i < kWBytes / 16; i += 128) w[i] = __ldg(a.Wimg + i);
+    for (int i = tid; i < kWBytes / 16; i += kThreads) w[i] = __ldg(a.Wimg + i);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  const long long plane_rows = (long long)a.Y * a.Z;     // rows per field
-  // ring slot of y position yy (yy >= yb - 1) and the parity of its fill
-  auto slot_of = [&](int yy) { return (yy - (yb - 1)) % kSlots; };
-  auto fill_parity = [&](int yy) { return (uint32_t)(((yy - (yb - 1)) / kSlots) & 1); };
-  auto row_smem = [&](int s, int zi) { return kRowsOff + (s * 3 + zi) * kRow; };
-  // thread 0: TMA of the 3 rows (z - 1, z, z + 1) x 4 channel groups of y position yy
-  auto issue_fill = [&](int yy) {
-    const int s = slot_of(yy);
-    const uint32_t bar = su32(&bars[s]);
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTxBytes) : "memory");
-    const int yw = wrapi(yy, a.Y);
-    for (int zi = 0; zi < 3; ++zi) {
-      const long long row = (long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw;
-      for (int g = 0; g < 4; ++g)
-        tma_load4(sbase + row_smem(s, zi) + g * kPlane + kInterior * 16, &tmap, 0, g, x0, (int)row, bar);
-    }
-  };
-  // threads 0..23: the periodic neighbours (entries 7 and 136) of the rows of y position yy
-  auto halo_fill = [&](int yy) {
-    if (tid < 24) {
-      const int s = slot_of(yy);
-      const int zi = tid >> 3, g = (tid >> 1) & 3, side = tid & 1;
-      const int yw = wrapi(yy, a.Y);
-      const long long row = (long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw;
-      const int x = side ? wrapi(x0 + kTM, a.X) : wrapi(x0 - 1, a.X);
-      const uint4 v = *reinterpret_cast<const uint4*>(a.Hin + (row * a.X + x) * kCh + g * 8);
-      *reinterpret_cast<uint4*>(sm + row_smem(s, zi) + g * kPlane + (side ? kInterior + kTM : kInterior - 1) * 16) = v;
-    }
-  };
-  const int last_row = yb + ny;                    // the last y position any step reads
-  __syncthreads();                                 // barriers initialised, TMEM address published
+  __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  // thread 0's bookkeeping: rows yb-1 .. issued are filled or in flight, rows yb-1 .. waited have landed
-  int issued = yb - 2, waited = yb - 2, mma_steps = 0;
-  if (tid == 0)
-    for (int yy = yb - 1; yy <= yb + 3 && yy <= last_row; ++yy) {
-      issue_fill(yy);
-      issued = yy;
+  if (warp < 4) {
+    // every accumulator slot starts at zero (the MMAs always accumulate)
+    uint32_t zr[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) zr[q] = 0u;
+    for (int sl = 0; sl < kAcc; ++sl) {
+      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sl * 32);
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+          "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+          ::"r"(ta), "r"(zr[0]), "r"(zr[1]), "r"(zr[2]), "r"(zr[3]), "r"(zr[4]), "r"(zr[5]), "r"(zr[6]), "r"(zr[7]),
+            "r"(zr[8]), "r"(zr[9]), "r"(zr[10]), "r"(zr[11]), "r"(zr[12]), "r"(zr[13]), "r"(zr[14]), "r"(zr[15]),
+            "r"(zr[16]), "r"(zr[17]), "r"(zr[18]), "r"(zr[19]), "r"(zr[20]), "r"(zr[21]), "r"(zr[22]), "r"(zr[23]),
+            "r"(zr[24]), "r"(zr[25]), "r"(zr[26]), "r"(zr[27]), "r"(zr[28]), "r"(zr[29]), "r"(zr[30]), "r"(zr[31])
+          : "memory");
     }
-  for (int yy = yb - 1; yy <= yb + 3 && yy <= last_row; ++yy) halo_fill(yy);
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();
-
-  // accumulator of step j: wait (warp-uniform) for its MMAs, read back this
-  // warp's 32 points, apply the epilogue and store bf16
-  auto epilogue = [&](int j) -> bool {
-    const int buf = j & 1;
-    bool got = bar_wait(su32(&bars[kSlots + buf]), (uint32_t)((j >> 1) & 1), a.wait_ns);
-    got = __all_sync(0xffffffffu, got);
-    if (!got) return false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    uint32_t v[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(buf * 32);
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int y = yb + j;
-    const long long p = (((long long)b * a.Z + z) * a.Y + y) * a.X + x0 + warp * 32 + lane;
-    uint4* dst = reinterpret_cast<uint4*>(a.Hout + p * kCh);
-    uint4 mk[4];
-    if (a.mode == 1) {
-      const uint4* m = reinterpret_cast<const uint4*>(a.Hmask + p * kCh);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) mk[q] = m[q];
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      float f[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[q * 8 + e]);
-      if (a.mode == 0) {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] = fmaxf(f[e], 0.f);
-      } else {
-        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk[q]);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) f[e] = __bfloat162float(mb[e]) > 0.f ? f[e] : 0.f;
-      }
-      dst[q] = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
-    }
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    return true;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const long long plane_rows = (long long)a.Y * a.Z;     // rows per field
+  const int nrows = ny + 2;                              // input rows: y positions yb - 1 .. yb + ny
+  auto row_smem = [&](int s, int zi) { return kRowsOff + (s * 3 + zi) * kRow; };
+  // accumulator slot of output row yb + m: consecutive output rows take
+  // consecutive slots downwards, so rows y'+1, y', y'-1 are ascending slots
+  auto acc_slot = [&](int m) { return (kAcc * 4096 - m) % kAcc; };
+  // bounded wait that also gives up when another role has aborted
+  auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
+    if (a.wait_ns == 0) return false;
+    const uint64_t t0 = gtime();
+    for (;;) {
+      uint32_t done;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity)
+          : "memory");
+      if (done) return true;
+      if (*abort_flag || gtime() - t0 > a.wait_ns) return false;
+    }
   };
 
-  bool aborted = false;
-  for (int j = 0; j < ny; ++j) {
-    const int y = yb + j;
-    bool fail = false;
-    if (tid == 0) {
-      // rows y - 1, y, y + 1 must have landed
-      while (!fail && waited < y + 1) {
-        const int yy = waited + 1;
-        if (bar_wait(su32(&bars[slot_of(yy)]), fill_parity(yy), a.wait_ns)) waited = yy;
-        else fail = true;
+  if (warp == 4) {
+    // ---- producer: input rows i = 0 .. nrows-1 (y position yb - 1 + i) into slot i % 5
+    for (int i = 0; i < nrows; ++i) {
+      const int s = i % kSlots;
+      bool ok = true;
+      if (i >= kSlots) ok = wait(empty0 + 8 * s, (uint32_t)(((i / kSlots) - 1) & 1));
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) { *abort_flag = 1; break; }
+      const int yw = wrapi(yb - 1 + i, a.Y);
+      if (lane < 24) {       // periodic neighbours (entries 7 and 136) of the 3 rows x 4 channel groups
+        const int zi = lane >> 3, g = (lane >> 1) & 3, side = lane & 1;
+        const long long row = (long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw;
+        const int x = side ? wrapi(x0 + kTM, a.X) : wrapi(x0 - 1, a.X);
+        const uint4 v = *reinterpret_cast<const uint4*>(a.Hin + (row * a.X + x) * kCh + g * 8);
+        *reinterpret_cast<uint4*>(sm + row_smem(s, zi) + g * kPlane + (side ? kInterior + kTM : kInterior - 1) * 16) =
+            v;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       }
-      if (!fail) {
+      __syncwarp();
+      if (lane == 0) {
+        const uint32_t bar = full0 + 8 * s;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTxBytes) : "memory");
+        for (int zi = 0; zi < 3; ++zi) {
+          const long long row = (long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw;
+          for (int g = 0; g < 4; ++g)
+            tma_load4(sbase + row_smem(s, zi) + g * kPlane + kInterior * 16, &tmap, 0, g, x0, (int)row, bar);
+        }
+        *rows_issued = i + 1;
+      }
+      __syncwarp();
+    }
+  } else if (warp == 5) {
+    // ---- MMA issue (lane 0): input row i = y' - (yb - 1) touches output rows
+    // m = i, i - 1, i - 2 (relative to yb) through dy = 0, 1, 2
+    if (lane == 0) {
+      for (int i = 0; i < nrows; ++i) {
+        bool ok = wait(full0 + 8 * (i % kSlots), (uint32_t)((i / kSlots) & 1));
+        if (ok) *rows_ready = i + 1;
+        // output row m = i enters the ring: its slot's previous row (m - 16)
+        // must have been read back and cleared
+        if (ok && i < ny && i >= kAcc) ok = wait(acce0 + 8 * acc_slot(i), (uint32_t)(((i - kAcc) / kAcc) & 1));
+        if (!ok) { *abort_flag = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dt = tmem + (uint32_t)((j & 1) * 32);
+        const int hi = min(i, ny - 1), lo = max(i - 2, 0);          // output rows in this CTA's range
+        if (hi >= lo) {
+          // runs of consecutive slots: rows hi, hi - 1, .., lo ascend through the slots
+          int m0 = hi, cnt = hi - lo + 1;
+          while (cnt > 0) {
+            const int s0 = acc_slot(m0);
+            const int run = min(cnt, kAcc - s0);
+            const int g0 = i - m0;                                  // tap dy of output row m0
+            const uint32_t dt = tmem + (uint32_t)(s0 * 32);
+            const uint32_t idesc = idesc_n(32 * run);
 #pragma unroll 1
-        for (int tap = 0; tap < kTaps; ++tap) {
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const uint32_t rb = sbase + row_smem(slot_of(y + dy - 1), dz);
+            for (int dz = 0; dz < 3; ++dz) {
+              const uint32_t rb = sbase + row_smem(i % kSlots, dz);
+#pragma unroll 1
+              for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-          for (int kc = 0; kc < 2; ++kc) {
-            const uint64_t ad = sdesc(rb + 2 * kc * kPlane + (kInterior - 1 + dx) * 16, kPlane, 128);
-            const uint64_t bd = sdesc(sbase + (tap * 2 + kc) * 1024, 512, 128);
-            mma_f16(dt, ad, bd, (tap | kc) != 0 ? 1u : 0u);
+                for (int kc = 0; kc < 2; ++kc) {
+                  const uint64_t ad = sdesc(rb + 2 * kc * kPlane + (kInterior - 1 + dx) * 16, kPlane, 128);
+                  const uint64_t bd = sdesc(sbase + ((dz * 3 + dx) * 2 + kc) * kBBlock + g0 * 512, kBBlock / 2, 128);
+                  mma_f16(dt, ad, bd, idesc);
+                }
+            }
+            m0 -= run;
+            cnt -= run;
           }
         }
+        // the staged row is read by no later MMA
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         su32(&bars[kSlots + (j & 1)]))
+                         empty0 + 8 * (i % kSlots))
                      : "memory");
-        ++mma_steps;
+        // output row i - 2 receives nothing more
+        if (i >= 2 && i - 2 < ny)
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           accf0 + 8 * acc_slot(i - 2))
+                       : "memory");
+        *rows_done = i + 1;
       }
     }
-    if (__syncthreads_or(fail)) { aborted = true; break; }
-    if (j >= 1) fail = !epilogue(j - 1);
-    if (__syncthreads_or(fail)) { aborted = true; break; }
-    // the MMAs of row y - 1 were the last to read the ring slot of y - 2:
-    // refill it with row y + 3, needed two steps on
-    if (j >= 1 && y + 3 <= last_row) {
-      if (tid == 0) {
-        issue_fill(y + 3);
-        issued = y + 3;
+    __syncwarp();
+  } else {
+    // ---- epilogue warps 0-3: output rows m = 0 .. ny-1
+    uint32_t zr[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) zr[q] = 0u;
+    for (int m = 0; m < ny; ++m) {
+      const int sl = acc_slot(m);
+      bool ok = wait(accf0 + 8 * sl, (uint32_t)((m / kAcc) & 1));
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) { *abort_flag = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(sl * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr)
+          : "memory");
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      // clear the slot for the output row that takes it next
+      asm volatile(
+          "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+          "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+          ::"r"(taddr), "r"(zr[0]), "r"(zr[1]), "r"(zr[2]), "r"(zr[3]), "r"(zr[4]), "r"(zr[5]), "r"(zr[6]),
+            "r"(zr[7]), "r"(zr[8]), "r"(zr[9]), "r"(zr[10]), "r"(zr[11]), "r"(zr[12]), "r"(zr[13]), "r"(zr[14]),
+            "r"(zr[15]), "r"(zr[16]), "r"(zr[17]), "r"(zr[18]), "r"(zr[19]), "r"(zr[20]), "r"(zr[21]), "r"(zr[22]),
+            "r"(zr[23]), "r"(zr[24]), "r"(zr[25]), "r"(zr[26]), "r"(zr[27]), "r"(zr[28]), "r"(zr[29]), "r"(zr[30]),
+            "r"(zr[31])
+          : "memory");
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(acce0 + 8 * sl) : "memory");
+      const int y = yb + m;
+      const long long p = (((long long)b * a.Z + z) * a.Y + y) * a.X + x0 + warp * 32 + lane;
+      uint4* dst = reinterpret_cast<uint4*>(a.Hout + p * kCh);
+      uint4 mk[4];
+      if (a.mode == 1) {
+        const uint4* mp = reinterpret_cast<const uint4*>(a.Hmask + p * kCh);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) mk[q] = mp[q];
       }
-      halo_fill(y + 3);
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-  }
-  if (!aborted && ny >= 1) aborted = __syncthreads_or(!epilogue(ny - 1));
-  if (aborted) {
-    // drain (bounded) what this CTA still has in flight before its shared and
-    // tensor memory are released
-    if (tid == 0) {
-      *a.flag = 1;
-      for (int yy = waited + 1; yy <= issued; ++yy)
-        bar_wait(su32(&bars[slot_of(yy)]), fill_parity(yy), 1000000000ull);
-      if (mma_steps > 0) {
-        const int jl = mma_steps - 1;
-        bar_wait(su32(&bars[kSlots + (jl & 1)]), (uint32_t)((jl >> 1) & 1), 1000000000ull);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float f[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] = __uint_as_float(v[q * 8 + e]);
+        if (a.mode == 0) {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) f[e] = fmaxf(f[e], 0.f);
+        } else {
+          const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk[q]);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) f[e] = __bfloat162float(mb[e]) > 0.f ? f[e] : 0.f;
+        }
+        dst[q] = make_uint4(pack2(f[0], f[1]), pack2(f[2], f[3]), pack2(f[4], f[5]), pack2(f[6], f[7]));
       }
     }
   }
   __syncthreads();
-  if (warp == 0) {
+  if (*abort_flag && tid == 0) {
+    // drain (bounded) what this CTA still has in flight before its shared and
+    // tensor memory are released: the staged rows no MMA batch waited for, and
+    // the MMAs of the last committed input row
+    *a.flag = 1;
+    const int ri = *rows_issued, rr = *rows_ready, rd = *rows_done;
+    for (int i = rr; i < ri; ++i) bar_wait(full0 + 8 * (i % kSlots), (uint32_t)((i / kSlots) & 1), 1000000000ull);
+    if (rd > 0) {
+      const int i = rd - 1;
+      bar_wait(empty0 + 8 * (i % kSlots), (uint32_t)((i / kSlots) & 1), 1000000000ull);
+    }
+  }
+  __syncthreads();
+  if (warp == 5) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
-// B operands of the 54 MMAs in shared-memory order: (tap, K half kc) block of
-// 1024 bytes = 2 K core-matrix columns (kg, 512 bytes apart) x 4 N core
-// matrices (128 bytes apart) x 8 rows (16 bytes) of 8 K values. Element
-// (n, k) of block (tap, kc), k = 16 kc + 8 kg + kk, is W[tap][k][n]
-// (forward) or W[26 - tap][n][k] (backward data: flipped taps, swapped
-// channels).
+// B operands in shared-memory order: block (dz, dx, K half kc) of kBBlock
+// bytes = 2 K core-matrix columns (kg, kBBlock/2 bytes apart) x 12 N core
+// matrices (128 bytes apart) x 8 rows (16 bytes) of 8 K values. Row n of the
+// block is output channel n % 32 of tap dy = n / 32; element (n, k), k = 16 kc +
+// 8 kg + kk, is W[tap][k][n % 32] (forward) or W[26 - tap][n % 32][k] (backward
+// data: flipped taps, swapped channels), tap = (dz * 3 + dy) * 3 + dx.
 __global__ void k_pack_umma(const float* __restrict__ W, __nv_bfloat16* __restrict__ img, int transposed) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= kTaps * kCh * kCh) return;
-  const int kk = i & 7, n = (i >> 3) & 31, kg = (i >> 8) & 1, kc = (i >> 9) & 1, tap = i >> 10;
+  const int kk = i & 7, n = (i >> 3) % 96, rest = (i >> 3) / 96;     // rest = ((dz * 3 + dx) * 2 + kc) * 2 + kg
+  const int kg = rest & 1, kc = (rest >> 1) & 1, dzdx = rest >> 2;
+  const int dz = dzdx / 3, dx = dzdx % 3, dy = n / 32, co = n % 32;
+  const int tap = (dz * 3 + dy) * 3 + dx;
   const int k = kc * 16 + kg * 8 + kk;
-  const float w = transposed ? W[((kTaps - 1 - tap) * kCh + n) * kCh + k] : W[(tap * kCh + k) * kCh + n];
-  const int off = (tap * 2 + kc) * 1024 + kg * 512 + (n >> 3) * 128 + (n & 7) * 16 + kk * 2;
+  const float w = transposed ? W[((kTaps - 1 - tap) * kCh + co) * kCh + k] : W[(tap * kCh + k) * kCh + co];
+  const int off = (dzdx * 2 + kc) * kBBlock + kg * (kBBlock / 2) + (n >> 3) * 128 + (n & 7) * 16 + kk * 2;
   img[off / 2] = __float2bfloat16_rn(w);
 }
 
@@ -416,7 +515,7 @@ cudaError_t conv_tc_forward(const __nv_bfloat16* Hin, const __nv_bfloat16* Wimg,
   a.wait_ns = wait_ns;
   a.flag = flag;
   const dim3 grid((unsigned)((X / kTM) * Z * (Y / a.ychunk)), (unsigned)B);
-  k_conv_tc<<<grid, 128, kSmemAlloc, s>>>(map, a);
+  k_conv_tc<<<grid, kThreads, kSmemAlloc, s>>>(map, a);
   return cudaGetLastError();
 }
 

@@ -14,12 +14,18 @@ equally valid evaluation that rounds differently. The spread of the oracle
 over a few shifts is its rounding sensitivity at the path's precision.
 
   * fields: the GPU must agree with the precision-matched oracle to
-    max(base, 10 * spread), base = 1e-5 (float32) or 1e-12 (float64);
-  * pass counts to a tolerance: exact if every shifted oracle run gives the
-    same count; otherwise within the observed range widened by that range on
-    each side, [min - R - 1, max + R + 1] with R = max - min (a count that is
-    chaotic under rounding -- BiCGSTAB at gamma = 0.01 spans tens of passes --
-    cannot be bracketed by the extremes of a few samples).
+    max(base, 3 x spread), base = 1e-5 (float32) or 1e-12 (float64), and
+    that tolerance has a ceiling: 1e-4 (float32), 1e-12 (float64). Measured,
+    the GPU's distance to the oracle is 0.4-1.7 x the oracle's spread in the
+    non-chaotic cases; a case whose spread would need more than the ceiling
+    is too chaotic for a field comparison at that pass count, and the helper
+    fails instead of widening the tolerance (such cases are compared at fewer
+    passes, and by the residual bound against the exact inverse);
+  * pass counts to a tolerance: exact where every shifted oracle run gives
+    the same count (count_exact, which fails when they differ); where equally
+    valid float64 evaluations give different counts (CG, SD and BiCGSTAB at
+    128^2, gamma = 0.1, to 1e-10), within the observed range without widening
+    (count_in_range).
 
 The oracle's code is not changed: these helpers wrap the filter function the
 oracle's solvers call.
@@ -34,6 +40,8 @@ import oracle
 import oracle.solvers as _osv
 
 BASE = {"f32": 1e-5, "f64": 1e-12}
+CAP = {"f32": 1e-4, "f64": 1e-12}
+MULT = 3.0
 SHIFTS = [(0, 0, 0), (1, 3, 2), (5, 2, 7), (11, 7, 3)]
 
 
@@ -78,25 +86,43 @@ def ensemble_runs(method, ub, gamma, tol, maxit, precision, u0=None, shifts=SHIF
     return out[0], out[1:]
 
 
-def field_tolerance(base, runs, precision):
+def field_tolerance(base, runs, precision, cap=None):
+    """(tolerance, spread): max(BASE, MULT x spread), failing when that
+    exceeds the ceiling (the case is too chaotic to compare fields)."""
     spread = max(rel(r.u, base.u) for r in runs)
-    return max(BASE[precision], 10.0 * spread), spread
+    ceiling = CAP[precision] if cap is None else cap
+    tol = max(BASE[precision], MULT * spread)
+    if tol > ceiling:
+        raise AssertionError("too chaotic for a field comparison: the oracle's spread over equally valid "
+                             "evaluations of G is %.3e, x%g = %.3e above the ceiling %.1e" % (spread, MULT, tol, ceiling))
+    return tol, spread
 
 
 def history_tolerance(base, runs, floor):
+    """Relative tolerance of the residual history: max(floor, MULT x the
+    oracle's own spread), at most 10 x floor."""
     n = len(base.history)
     spread = max(float(np.max(np.abs(r.history[:n] / base.history[: len(r.history)] - 1)))
                  for r in runs if len(r.history) == n)
-    return max(floor, 10.0 * spread)
+    tol = max(floor, MULT * spread)
+    if tol > 10 * floor:
+        raise AssertionError("too chaotic for a history comparison: spread %.3e" % spread)
+    return tol
 
 
-def count_ok(n_gpu, base, runs):
+def count_exact(n_gpu, base, runs):
+    """(ok, counts): the GPU's pass count equals the oracle's, which every
+    shifted run must agree on."""
     counts = [base.iterations] + [r.iterations for r in runs]
-    lo, hi = min(counts), max(counts)
-    if lo == hi:
-        return n_gpu == lo, counts
-    r = hi - lo
-    return lo - r - 1 <= n_gpu <= hi + r + 1, counts
+    if min(counts) != max(counts):
+        raise AssertionError("the oracle's pass count varies between equally valid evaluations: %s" % counts)
+    return n_gpu == counts[0], counts
+
+
+def count_in_range(n_gpu, base, runs):
+    """(ok, counts): min <= n_gpu <= max over the oracle's shifted runs."""
+    counts = [base.iterations] + [r.iterations for r in runs]
+    return min(counts) <= n_gpu <= max(counts), counts
 
 
 # --- the spectral-space variant ------------------------------------------------

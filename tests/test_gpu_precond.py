@@ -8,9 +8,10 @@ products, and M amplifies them at the highest wavenumbers by up to
 1 + 4 sum_d c_d (c_d = 1/(pi gamma)^2 on cubic grids: ~8000 at gamma = 0.01).
 Fields are therefore judged, from the first pass on, with the same
 precision-matched ensemble as the other solvers (tests/parity_tools.py):
-within max(1e-5 float32 / 1e-12 float64, 10 x the oracle's spread over
-equally valid shifted evaluations of G); pass counts exact when that
-oracle's count is stable and within its spread otherwise.
+within max(1e-5 float32 / 1e-12 float64, 3 x the oracle's spread over
+equally valid shifted evaluations of G), never above 1e-4 / 1e-12; pass
+counts exact (the preconditioned iteration is well conditioned, and every
+shifted oracle run must agree on the count).
 """
 
 import numpy as np
@@ -18,7 +19,7 @@ import pytest
 
 import oracle
 from synth import fields
-from parity_tools import count_ok, ensemble_runs, field_tolerance, history_tolerance
+from parity_tools import count_exact, ensemble_runs, field_tolerance, history_tolerance
 
 pytestmark = pytest.mark.gpu
 
@@ -62,9 +63,11 @@ def test_one_pass_on_wrapping_tiles(gad):
         np.testing.assert_allclose(res.history[0, :2], ref.history, rtol=1e-5)
 
 
-@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((96, 128), 0.1), ((256, 256), 0.01),
-                                         ((2048, 2048), 0.01), ((32, 32, 32), 0.1), ((24, 48, 32), 0.1),
-                                         ((64, 64, 64), 0.01)])
+# gamma = 0.01 is compared in float64 (below): there M amplifies float32
+# rounding at the top wavenumbers by up to ~8000, and the float32 oracle's own
+# spread over equally valid evaluations is 1e-4 - 3e-4 already after one pass
+# (measured), above the 1e-4 ceiling
+@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((96, 128), 0.1), ((32, 32, 32), 0.1), ((24, 48, 32), 0.1)])
 @pytest.mark.parametrize("npass", [1, 5, 12])
 def test_fixed_passes_f32(gad, shape, gamma, npass):
     _, ub = _problem(shape, 3, gamma)
@@ -83,15 +86,15 @@ def test_fixed_passes_f32(gad, shape, gamma, npass):
                                atol=H_ATOL)
 
 
-def test_fixed_passes_f64(gad):
-    _, ub = _problem((128, 128), 0, 0.1, dtype=np.float64)
+@pytest.mark.parametrize("shape,gamma", [((128, 128), 0.1), ((256, 256), 0.01), ((64, 64, 64), 0.01)])
+def test_fixed_passes_f64(gad, shape, gamma):
+    _, ub = _problem(shape, 0, gamma, dtype=np.float64)
     for npass in (1, 5, 12):
-        res = gad.deconvolve(_to_gpu(ub), 0.1, method="pcg", tol=0.0, maxit=npass)
-        base, runs = ensemble_runs("pcg", ub, 0.1, 0.0, npass, "f64")
+        res = gad.deconvolve(_to_gpu(ub), gamma, method="pcg", tol=0.0, maxit=npass, ndim=len(shape))
+        base, runs = ensemble_runs("pcg", ub, gamma, 0.0, npass, "f64")
         tol, spread = field_tolerance(base, runs, "f64")
-        if npass == 1:
-            tol = 1e-12
-        assert _rel(res.u.cpu().numpy(), base.u) < tol, (npass, spread)
+        err = _rel(res.u.cpu().numpy(), base.u)
+        assert err < 1e-12, "passes %d: error %.3e, oracle spread %.3e" % (npass, err, spread)
         np.testing.assert_allclose(res.history[0, :npass + 1], base.history, rtol=history_tolerance(base, runs, 1e-11))
 
 
@@ -105,7 +108,7 @@ def test_config1_f64_to_tolerance(gad, gamma):
     res = gad.deconvolve(_to_gpu(ub), gamma, method="pcg", tol=1e-10, maxit=500, true_residual=True)
     base, runs = ensemble_runs("pcg", ub, gamma, 1e-10, 500, "f64")
     assert int(res.status[0]) == gad.AD_OK == base.status
-    ok, counts = count_ok(int(res.iterations[0]), base, runs)
+    ok, counts = count_exact(int(res.iterations[0]), base, runs)
     assert ok, (int(res.iterations[0]), counts)
     assert int(res.iterations[0]) <= 25
     tol, spread = field_tolerance(base, runs, "f64")
@@ -123,12 +126,14 @@ def test_f32_to_tolerance_counts(gad, shape, gamma):
     base, runs = ensemble_runs("pcg", ub.astype(np.float64), gamma, tol, 500, "f32")
     n_gpu = int(res.iterations[0])
     assert int(res.status[0]) == gad.AD_OK
-    ok, counts = count_ok(n_gpu, base, runs)
+    ok, counts = count_exact(n_gpu, base, runs)
     assert ok, (n_gpu, counts)
     assert res.history[0, n_gpu] <= tol
     assert res.true_residual[0] < 20 * tol
-    tolf, spread = field_tolerance(base, runs, "f32")
-    assert _rel(res.u.double().cpu().numpy(), base.u) < tolf, spread
+    if gamma >= 0.1:                  # see test_fixed_passes_f32 for gamma = 0.01
+        tolf, spread = field_tolerance(base, runs, "f32")
+        err = _rel(res.u.double().cpu().numpy(), base.u)
+        assert err < tolf, "error %.3e, tolerance %.3e, oracle spread %.3e" % (err, tolf, spread)
     uex = oracle.exact_inverse(ub.astype(np.float64), gamma)
     ref = np.linalg.norm(ub.astype(np.float64) - oracle.filter_field(ub.astype(np.float64), gamma))
     gmin = oracle.transfer_function(shape, gamma).min()
@@ -212,7 +217,7 @@ def test_initial_guess(gad):
     u0 = 0.5 * (ub + u)
     res = gad.deconvolve(_to_gpu(ub), 0.1, method="pcg", tol=1e-9, maxit=200, u0=_to_gpu(u0))
     base, runs = ensemble_runs("pcg", ub, 0.1, 1e-9, 200, "f64", u0=u0)
-    ok, counts = count_ok(int(res.iterations[0]), base, runs)
+    ok, counts = count_exact(int(res.iterations[0]), base, runs)
     assert ok, (int(res.iterations[0]), counts)
     assert res.history[0, 0] == pytest.approx(base.history[0], rel=1e-12) and res.history[0, 0] < 1.0
     assert _rel(res.u.cpu().numpy(), oracle.exact_inverse(ub, 0.1)) < 1e-6
@@ -232,10 +237,15 @@ def test_bench_workload_full_size(gad):
     assert np.all(res.status == gad.AD_OK), res.status
     assert np.all(res.iterations <= 20), res.iterations
     assert np.all(res.true_residual < 50e-6)
+    # three fixed passes against the float32 oracle on one field: the residual
+    # history (a global norm; the float32 field itself is too sensitive at
+    # gamma = 0.01 for a 1e-4 comparison, see test_fixed_passes_f32). The
+    # residual drops 5000-fold in the first pass, so its float32 evaluation
+    # carries an absolute error of a few float32 epsilons of ||r_0||: the
+    # normalised history is compared to 2e-7 absolute (3.4 eps32)
     res = gad.deconvolve(t, 0.01, method="pcg", tol=0.0, maxit=3, ndim=2)
-    base, runs = ensemble_runs("pcg", ub[9].astype(np.float64), 0.01, 0.0, 3, "f32")
-    tolf, spread = field_tolerance(base, runs, "f32")
-    assert _rel(res.u[9].double().cpu().numpy(), base.u) < tolf, spread
+    base, _ = ensemble_runs("pcg", ub[9].astype(np.float64), 0.01, 0.0, 3, "f32", shifts=[(0, 0, 0)] * 2)
+    np.testing.assert_allclose(res.history[9, :4], base.history, rtol=1e-5, atol=2e-7)
 
 
 def test_bounded_wait_times_out_cleanly(gad):
@@ -260,8 +270,7 @@ def test_bounded_wait_times_out_cleanly(gad):
 
 # --- preconditioned CG in spectral space (AD_SPECTRAL | AD_PRECOND) ----------
 
-@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((96, 128), 0.1), ((256, 256), 0.01),
-                                         ((32, 32, 32), 0.1), ((24, 48, 32), 0.1), ((64, 64, 64), 0.01)])
+@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((96, 128), 0.1), ((32, 32, 32), 0.1), ((24, 48, 32), 0.1)])
 @pytest.mark.parametrize("npass", [1, 5, 12])
 def test_spectral_fixed_passes_f32(gad, shape, gamma, npass):
     from parity_tools import ensemble_runs_spectral
@@ -273,6 +282,19 @@ def test_spectral_fixed_passes_f32(gad, shape, gamma, npass):
     assert _rel(res.u.double().cpu().numpy(), base.u) < tol, (_rel(res.u.double().cpu().numpy(), base.u), spread)
     np.testing.assert_allclose(res.history[0, :npass + 1], base.history, rtol=history_tolerance(base, runs, 1e-5),
                                atol=H_ATOL)
+
+
+@pytest.mark.parametrize("shape,gamma", [((128, 128), 0.1), ((256, 256), 0.01), ((64, 64, 64), 0.01)])
+def test_spectral_fixed_passes_f64(gad, shape, gamma):
+    from parity_tools import ensemble_runs_spectral
+    _, ub = _problem(shape, 0, gamma, dtype=np.float64)
+    for npass in (1, 5, 12):
+        res = gad.deconvolve(_to_gpu(ub), gamma, method="pcg", tol=0.0, maxit=npass, ndim=len(shape),
+                             space="spectral")
+        base, runs = ensemble_runs_spectral("pcg", ub, gamma, 0.0, npass, "f64")
+        tol, spread = field_tolerance(base, runs, "f64")
+        err = _rel(res.u.cpu().numpy(), base.u)
+        assert err < 1e-12, "passes %d: error %.3e, oracle spread %.3e" % (npass, err, spread)
 
 
 @pytest.mark.parametrize("gamma", [0.1, 0.01])
@@ -287,7 +309,7 @@ def test_spectral_f64_to_tolerance(gad, gamma):
                          space="spectral")
     base, runs = ensemble_runs_spectral("pcg", ub, gamma, 1e-10, 500, "f64")
     assert int(res.status[0]) == gad.AD_OK
-    ok, counts = count_ok(int(res.iterations[0]), base, runs)
+    ok, counts = count_exact(int(res.iterations[0]), base, runs)
     assert ok, (int(res.iterations[0]), counts)
     assert _rel(res.u.cpu().numpy(), oracle.exact_inverse(ub, gamma)) < 1e-7
     assert res.true_residual[0] < 2e-10
@@ -307,7 +329,7 @@ def test_spectral_to_tolerance_matches_physical(gad, shape, gamma):
     assert int(a.status[0]) == int(b.status[0]) == gad.AD_OK
     assert abs(int(a.iterations[0]) - int(b.iterations[0])) <= 1
     base, runs = ensemble_runs_spectral("pcg", ub.astype(np.float64), gamma, 1e-6, 500, "f32")
-    ok, counts = count_ok(int(b.iterations[0]), base, runs)
+    ok, counts = count_exact(int(b.iterations[0]), base, runs)
     assert ok, (int(b.iterations[0]), counts)
     ref = np.linalg.norm(ub.astype(np.float64) - oracle.filter_field(ub.astype(np.float64), gamma))
     gmin = oracle.transfer_function(shape, gamma).min()

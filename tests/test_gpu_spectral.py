@@ -4,11 +4,12 @@ CPU oracle's spectral-space mode (pinned to its physical-space algorithms in
 tests/test_oracle_solvers.py):
   * one pass: relative L2 <= 1e-5 (float32) or <= 1e-12 (float64) against
     the float64 oracle;
-  * more passes and tolerance-stopped solves: within max(1e-5 or 1e-12,
-    10 x the spread of the precision-matched spectral oracle over periodic
-    shifts of the input -- see tests/parity_tools.py);
-  * iteration counts: exact when that oracle's count is the same for every
-    shift, else within its spread widened by the spread (+1).
+  * more passes: within max(1e-5 or 1e-12, 3 x the spread of the
+    precision-matched spectral oracle over periodic shifts of the input),
+    never above 1e-4 (float32) or 1e-12 (float64), at pass counts where that
+    is meaningful (tests/parity_tools.py);
+  * iteration counts: exact where every shifted oracle run agrees; within
+    the observed range where equally valid float64 evaluations differ.
 """
 
 import numpy as np
@@ -16,7 +17,7 @@ import pytest
 
 import oracle
 from synth import fields
-from parity_tools import count_ok, field_tolerance, history_tolerance
+from parity_tools import count_exact, count_in_range, field_tolerance, history_tolerance
 from parity_tools import ensemble_runs_spectral as ensemble_runs
 
 pytestmark = pytest.mark.gpu
@@ -68,20 +69,25 @@ def test_fixed_passes_f32(gad, method, shape, gamma, npass):
                                rtol=history_tolerance(base, runs, 1e-5))
 
 
-# gamma = 0.01 is compared at 5 passes and to tolerance (below), not at 20
-# fixed passes: there (condition number 2e4) equally valid float32 runs of
-# BiCGSTAB drift apart by 15% after 20 passes and a single residual spike
-# decides where a run stands, so the fixed-pass field says nothing about
-# correctness; the tolerance-stopped solve is checked against the exact
-# inverse with a rigorous bound instead.
-@pytest.mark.parametrize("method", METHODS)
-@pytest.mark.parametrize("shape,gamma", [((64, 64), 0.1), ((128, 96), 0.1), ((32, 32, 32), 0.1)])
-def test_twenty_passes_f32(gad, method, shape, gamma):
+# Longer float32 runs where the spectral oracle's own spread stays below the
+# 1e-4 ceiling (the same chaos boundary as in physical space: Van Cittert
+# everywhere, the Krylov methods at gamma = 0.1 to 10 passes, SD and CG on
+# the 2D grids to 20); gamma = 0.01 is compared at 5 passes and, to tolerance,
+# against the exact inverse with a rigorous bound (below).
+LONG_F32 = ([(m, sh, 0.1, 10) for m in METHODS for sh in ((64, 64), (128, 96))] +
+            [(m, (32, 32, 32), 0.1, 10) for m in ("vancittert", "sd")] +
+            [("vancittert", sh, 0.1, 20) for sh in ((64, 64), (128, 96), (32, 32, 32))] +
+            [("sd", (64, 64), 0.1, 20), ("sd", (128, 96), 0.1, 20), ("cg", (128, 96), 0.1, 20)])
+
+
+@pytest.mark.parametrize("method,shape,gamma,npass", LONG_F32)
+def test_longer_fixed_passes_f32(gad, method, shape, gamma, npass):
     _, ub = _problem(shape, 3, gamma)
-    res = _solve(gad, ub, gamma, method=method, tol=0.0, maxit=20)
-    base, runs = ensemble_runs(method, ub.astype(np.float64), gamma, 0.0, 20, "f32")
+    res = _solve(gad, ub, gamma, method=method, tol=0.0, maxit=npass)
+    base, runs = ensemble_runs(method, ub.astype(np.float64), gamma, 0.0, npass, "f32")
     tol, spread = field_tolerance(base, runs, "f32")
-    assert _rel(res.u.double().cpu().numpy(), base.u) < tol, spread
+    err = _rel(res.u.double().cpu().numpy(), base.u)
+    assert err < tol, "error %.3e, tolerance %.3e, oracle spread %.3e" % (err, tol, spread)
 
 
 def test_van_cittert_closed_form_f32(gad):
@@ -97,37 +103,61 @@ def test_van_cittert_closed_form_f32(gad):
         assert _rel(res.u.double().cpu().numpy(), ref) < 1e-5, n
 
 
+F64_PASSES = {"vancittert": (1, 5, 20), "sd": (1, 5, 20), "cg": (1, 5, 20), "bicgstab": (1, 5, 12)}
+
+
 @pytest.mark.parametrize("method", METHODS)
 def test_fixed_passes_f64(gad, method):
     _, ub = _problem((128, 128), 0, 0.1, dtype=np.float64)
-    for npass in (1, 5, 20):
+    for npass in F64_PASSES[method]:
         res = _solve(gad, ub, 0.1, method=method, tol=0.0, maxit=npass)
         base, runs = ensemble_runs(method, ub, 0.1, 0.0, npass, "f64")
         tol, spread = field_tolerance(base, runs, "f64")
-        if npass == 1:
-            tol = 1e-12
-        assert _rel(res.u.cpu().numpy(), base.u) < tol, (npass, spread)
-        np.testing.assert_allclose(res.history[0, :npass + 1], base.history,
-                                   rtol=history_tolerance(base, runs, 1e-11))
+        err = _rel(res.u.cpu().numpy(), base.u)
+        assert err < 1e-12, "passes %d: error %.3e, oracle spread %.3e" % (npass, err, spread)
+        np.testing.assert_allclose(res.history[0, :npass + 1], base.history, rtol=1e-9)
 
 
 @pytest.mark.parametrize("method", METHODS)
 def test_config1_f64_to_tolerance(gad, method):
-    """128^2 float64 vorticity, gamma = 0.1, to relative residual 1e-10."""
+    """128^2 float64 vorticity, gamma = 0.1, to relative residual 1e-10: Van
+    Cittert's pass count exact and its field within 1e-12; for the Krylov
+    methods the count within the range of equally valid evaluations and the
+    field within 1e-10 of a same-count oracle run; for all the exact inverse
+    within the residual bound."""
     spec = lambda k: fields.spectrum_2d_kraichnan(k, kp=8.0)
     u = fields.random_scalar_field((128, 128), 0, spec)
     ub = oracle.filter_field(u, 0.1)
     maxit = 5000 if method in ("vancittert", "sd") else 1000
     res = _solve(gad, ub, 0.1, method=method, tol=1e-10, maxit=maxit, true_residual=True)
     base, runs = ensemble_runs(method, ub, 0.1, 1e-10, maxit, "f64")
+    n_gpu = int(res.iterations[0])
+    got = res.u.cpu().numpy()
     assert int(res.status[0]) == gad.AD_OK == base.status
-    ok, counts = count_ok(int(res.iterations[0]), base, runs)
-    assert ok, (int(res.iterations[0]), counts)
-    tol, spread = field_tolerance(base, runs, "f64")
-    assert _rel(res.u.cpu().numpy(), base.u) < tol, spread
-    assert _rel(res.u.cpu().numpy(), oracle.exact_inverse(ub, 0.1)) < 1e-7
-    assert res.history[0, int(res.iterations[0])] <= 1e-10
+    if method == "vancittert":
+        ok, counts = count_exact(n_gpu, base, runs)
+        assert ok, (n_gpu, counts)
+        assert _rel(got, base.u) < 1e-12
+    elif method in ("cg", "sd"):
+        ok, counts = count_in_range(n_gpu, base, runs)
+        assert ok, (n_gpu, counts)
+        same = [_rel(got, r.u) for r in [base] + runs if r.iterations == n_gpu]
+        assert all(e < 1e-10 for e in same), same
+    else:
+        # BiCGSTAB: count and final iterate chaotic even in float64 (see the
+        # physical-space test); the first 12 passes and the bounds pin it
+        n = min(n_gpu, base.iterations, 12)
+        np.testing.assert_allclose(res.history[0, :n + 1], base.history[:n + 1], rtol=1e-9)
+    uex = oracle.exact_inverse(ub, 0.1)
+    ref = np.linalg.norm(ub - oracle.filter_field(ub, 0.1))
+    gmin = oracle.transfer_function((128, 128), 0.1).min()
+    assert np.linalg.norm(got - uex) <= 1.05 * res.true_residual[0] * ref / gmin
+    assert _rel(got, uex) < 1e-7
+    assert res.history[0, n_gpu] <= 1e-10
     assert res.true_residual[0] < 2e-10
+
+
+EXACT_COUNT_F32 = {("cg", (256, 256), 0.1), ("cg", (64, 64, 64), 0.1)}
 
 
 @pytest.mark.parametrize("method", ["cg", "bicgstab"])
@@ -136,11 +166,13 @@ def test_f32_to_tolerance_counts(gad, method, shape, gamma):
     _, ub = _problem(shape, 1, gamma)
     tol = 1e-6
     res = _solve(gad, ub, gamma, method=method, tol=tol, maxit=2000, true_residual=True)
-    base, runs = ensemble_runs(method, ub.astype(np.float64), gamma, tol, 2000, "f32")
     n_gpu = int(res.iterations[0])
     assert int(res.status[0]) == gad.AD_OK
-    ok, counts = count_ok(n_gpu, base, runs)
-    assert ok, (n_gpu, counts)
+    if (method, shape, gamma) in EXACT_COUNT_F32:
+        # the spectral oracle's nine shifted runs differ by at most one pass here
+        base, runs = ensemble_runs(method, ub.astype(np.float64), gamma, tol, 2000, "f32")
+        ok, counts = count_in_range(n_gpu, base, runs)
+        assert ok and max(counts) - min(counts) <= 1, (n_gpu, counts)
     assert res.history[0, n_gpu] <= tol
     assert res.true_residual[0] < 20 * tol
     # against the exact (Fourier) inverse: ||u - u_ex|| <= ||r_true|| / G_hat_min
@@ -192,8 +224,7 @@ def test_initial_guess_f64(gad):
     u0 = 0.5 * (ub + u)
     res = _solve(gad, ub, 0.1, method="bicgstab", tol=1e-9, maxit=500, u0=_to_gpu(u0))
     base, runs = ensemble_runs("bicgstab", ub, 0.1, 1e-9, 500, "f64", u0=u0)
-    ok, counts = count_ok(int(res.iterations[0]), base, runs)
-    assert ok, (int(res.iterations[0]), counts)
+    np.testing.assert_allclose(res.history[0, :13], base.history[:13], rtol=1e-9)
     assert res.history[0, 0] == pytest.approx(base.history[0], rel=1e-12)
     assert res.history[0, int(res.iterations[0])] <= 1e-9
     res1 = _solve(gad, ub, 0.1, method="bicgstab", tol=0.0, maxit=1, u0=_to_gpu(u0))
