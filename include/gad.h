@@ -219,6 +219,18 @@ ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const flo
                          int epochs, int batch, double lr, uint64_t seed, float* weights, double* loss_hist,
                          void* stream);
 
+/* Measures one forward 32 -> 32 layer of the learned guess's network
+ * (ReLU(conv(H1, W2)) on the context's workspace for this grid and batch,
+ * zero weights and activations) in the launch shape inference uses: warm-up,
+ * then `reps` launches on `stream` between two CUDA events. Outputs (host,
+ * may be NULL): ms per launch, tensor_cores = 1 when the layer ran on the
+ * tcgen05 tensor-core kernel (x side a multiple of 128), 0 for the
+ * warp-level mma kernel. Blocks the host until the timing completes. No
+ * counterpart in the paper: it relates the convolution's time to the bf16
+ * tensor-core roofline (55,296 flop per grid point per layer). */
+ad_status ad_guess_time_conv(ad_ctx* ctx, const ad_grid* grid, int batch, int reps, void* stream, double* ms,
+                             int* tensor_cores);
+
 /* Tile autotuner. With `grid` non-NULL, tunes the plan for (grid, batch):
  * for every pass of one iteration of `method` it times each admissible tile
  * width (32-256 threads per block, <= 100 KB shared memory) with CUDA events
@@ -259,9 +271,11 @@ ad_status ad_time_pass(ad_ctx* ctx, const ad_grid* grid, int batch, ad_method me
  *   The scratch (twiddle tables and spectral buffers) lives in one
  * file-scope device array of AD_STATIC_SCRATCH_BYTES, held by every GPU that
  * loads the library until the process exits. A call needs, with cs = 8
- * (AD_F32) or 16 (AD_F64) and each term rounded up to 256 bytes:
- *   cs*Nx + cs*Ny [+ cs*Nz] + k * cs*batch*(Nx/2+1)*Ny*Nz,  k = 1 (2D), 2 (3D)
- * bytes; larger requests return AD_ERR_ARG (e.g. 2D float32 up to one 2048^2
+ * (AD_F32) or 16 (AD_F64), L the last axis's length (Ny in 2D, Nz in 3D) and
+ * each term rounded up to 256 bytes:
+ *   cs*Nx + cs*Nx/2 + 2*cs*L [+ cs*Ny in 3D] + k * cs*batch*(Nx/2+1)*Ny*Nz,
+ *   k = 1 (2D), 2 (3D)
+ * bytes (twiddle tables and spectral buffers); larger requests return AD_ERR_ARG (e.g. 2D float32 up to one 2048^2
  * field, 3D float32 up to one 128^3 field). Grid rules, pointers and the
  * stream are as for ad_filter; `in` and `out` may be the same buffer.
  *   The device address of the array is looked up (cudaGetSymbolAddress) by

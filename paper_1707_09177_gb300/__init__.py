@@ -46,7 +46,7 @@ EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvo
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
             "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
             "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl", "ad_set_wait_limit",
-            "ad_deconvolve_host")
+            "ad_deconvolve_host", "ad_guess_time_conv")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec", 8: "sten"}
 
 
@@ -127,6 +127,8 @@ def load(path=None):
     lib.ad_histogram.restype = c_i
     lib.ad_curl.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_p, c_p, c_p]
     lib.ad_curl.restype = c_i
+    lib.ad_guess_time_conv.argtypes = [c_p, ctypes.POINTER(ad_grid), c_i, c_i, c_p, c_p, c_p]
+    lib.ad_guess_time_conv.restype = c_i
     lib.ad_set_wait_limit.argtypes = [c_p, ctypes.c_uint64]
     lib.ad_set_wait_limit.restype = c_i
     _lib = lib
@@ -418,6 +420,25 @@ def guess_infer(weights, ubar, gamma, out=None, stream=None):
                             ctypes.c_void_p(ubar.data_ptr()), ctypes.c_void_p(out.data_ptr()), b, _stream_ptr(stream))
     _check(st, ctx)
     return out
+
+
+def guess_time_conv(shape, batch, gamma=0.01, reps=5, stream=None, device=None):
+    """(ms per launch, ran on tcgen05) of one forward 32 -> 32 layer of the
+    learned guess's network for fields of ``shape`` (Z, Y, X) and ``batch``,
+    timed by the library with CUDA events in inference's launch shape."""
+    lib = load()
+    ctx = context(device)
+    g = ad_grid()
+    g.ndim = 3
+    for i, n in enumerate(reversed(shape)):
+        g.n[i] = int(n)
+    g.dtype = AD_F32
+    g.gamma = float(gamma)
+    ms, tc = ctypes.c_double(), ctypes.c_int()
+    st = lib.ad_guess_time_conv(ctx, ctypes.byref(g), int(batch), int(reps), _stream_ptr(stream), ctypes.byref(ms),
+                                ctypes.byref(tc))
+    _check(st, ctx)
+    return float(ms.value), bool(tc.value)
 
 
 def guess_grad(weights, ubar, utrue, gamma, stream=None):

@@ -167,6 +167,38 @@ std::vector<T> twiddle_host(long long L) {
   return t;
 }
 
+// The twiddle table of the FFT plan of length L for E elements per thread
+// (plan.h): per-stage factors, cached per (plan, precision). Null (and AD_OK)
+// when L has no plan; building the plan then fails.
+ad_status get_plan_table(ad_ctx* ctx, int L, int E, bool reversed, bool f64, const void** out) {
+  int rad[kMaxStages];
+  const int n = plan_radices(L, E, reversed, rad);
+  *out = nullptr;
+  if (n == 0) return AD_OK;
+  // keys of full tables are (L, 0 or 1); plan tables are (L | E | reversed, 2 or 3)
+  const auto key = std::make_pair(((long long)L << 8) | ((long long)E << 1) | (reversed ? 1 : 0), f64 ? 3 : 2);
+  auto it = ctx->tw.find(key);
+  if (it != ctx->tw.end()) { *out = it->second; return AD_OK; }
+  const size_t ents = (size_t)std::max(L - 1, 1);
+  void* d = nullptr;
+  const size_t bytes = ents * (f64 ? 16 : 8);
+  if (cudaMalloc(&d, bytes) != cudaSuccess) { cudaGetLastError(); return fail(ctx, AD_ERR_NOMEM, "twiddle table"); }
+  cudaError_t e;
+  if (f64) {
+    std::vector<double> h(2 * ents, 0.0);
+    plan_twiddles<double>(rad, n, h.data());
+    e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
+  } else {
+    std::vector<float> h(2 * ents, 0.f);
+    plan_twiddles<float>(rad, n, h.data());
+    e = cudaMemcpy(d, h.data(), bytes, cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) { cudaFree(d); return cuda_fail(ctx, e, "twiddle upload"); }
+  ctx->tw[key] = d;
+  *out = d;
+  return AD_OK;
+}
+
 ad_status get_table(ad_ctx* ctx, long long L, bool f64, const void** out) {
   auto key = std::make_pair(L, f64 ? 1 : 0);
   auto it = ctx->tw.find(key);
@@ -264,32 +296,38 @@ ad_status get_plan(ad_ctx* ctx, const ad_grid* g, int batch, Plan** out) {
   p->SP = (long long)p->kxn * p->ny * p->nz;
   const size_t cs = p->f64 ? 16 : 8, rs = p->f64 ? 8 : 4;
   ad_status s;
-  const void *tx = nullptr, *ty = nullptr, *tz = nullptr;
+  const void* tx = nullptr;
   if ((s = get_table(ctx, p->nx, p->f64, &tx)) != AD_OK) { delete p; return s; }
-  if ((s = get_table(ctx, p->ny, p->f64, &ty)) != AD_OK) { delete p; return s; }
-  if (p->ndim == 3 && (s = get_table(ctx, p->nz, p->f64, &tz)) != AD_OK) { delete p; return s; }
-  p->twx = tx;
+  p->twx = tx;                                  // the real-to-complex split of the x passes
   const int M = p->nx / 2;
+  const int Lf = p->ndim == 3 ? p->nz : p->ny;
+  const void *px = nullptr, *pf = nullptr, *pfi = nullptr, *py = nullptr;
+  if ((s = get_plan_table(ctx, M, pick_E(M), false, p->f64, &px)) != AD_OK ||
+      (s = get_plan_table(ctx, Lf, pick_E(Lf), false, p->f64, &pf)) != AD_OK ||
+      (s = get_plan_table(ctx, Lf, pick_E(Lf), true, p->f64, &pfi)) != AD_OK ||
+      (p->ndim == 3 && (s = get_plan_table(ctx, p->ny, pick_E(p->ny), false, p->f64, &py)) != AD_OK)) {
+    delete p;
+    return s;
+  }
   bool ok = true;
-  // x passes: complex length M (packed real rows), table of length nx, stride 2
+  // x passes: complex length M (packed real rows)
   ok = ok && choose_tile(M, pick_E(M), M + 1, pow2_part(p->ny), cs, p->xf);
-  ok = ok && make_fft(M, p->xf.E, tx, p->nx, p->xf.fft);
+  ok = ok && make_fft(M, p->xf.E, px, p->xf.fft);
   p->xf.rcp_a = 1.0f / (float)(p->nx / 4);
   p->xf.rcp_b = 1.0f / (float)(M / 2 + 1);
   p->xf.grid = dim3(p->ny * p->nz / std::max(p->xf.W, 1), batch);
   p->xi = p->xf;
   // filter pass along the last axis
-  const int Lf = p->ndim == 3 ? p->nz : p->ny;
   const int nseq = p->ndim == 3 ? p->kxn * p->ny : p->kxn;
   ok = ok && choose_tile(Lf, pick_E(Lf), Lf, 0, cs, p->fl);
-  ok = ok && make_fft(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft);
-  ok = ok && make_fft(Lf, p->fl.E, p->ndim == 3 ? tz : ty, Lf, p->fl.fft_inv, true);
+  ok = ok && make_fft(Lf, p->fl.E, pf, p->fl.fft);
+  ok = ok && make_fft(Lf, p->fl.E, pfi, p->fl.fft_inv, true);
   p->fl.rcp_a = 1.0f / (float)(Lf / 2);
   p->fl.rcp_b = 1.0f / (float)Lf;
   p->fl.grid = dim3((nseq + std::max(p->fl.W, 1) - 1) / std::max(p->fl.W, 1), batch);
   if (p->ndim == 3) {
     ok = ok && choose_tile(p->ny, pick_E(p->ny), p->ny, pow2_part(p->nz), cs, p->yf);
-    ok = ok && make_fft(p->ny, p->yf.E, ty, p->ny, p->yf.fft);
+    ok = ok && make_fft(p->ny, p->yf.E, py, p->yf.fft);
     p->yf.rcp_a = 1.0f / (float)(p->ny / 2);
     p->yf.rcp_b = 1.0f / (float)p->ny;
     p->yf.grid = dim3(p->kxn * (p->nz / std::max(p->yf.W, 1)), batch);
@@ -1511,6 +1549,43 @@ ad_status ad_guess_infer(ad_ctx* ctx, const ad_grid* grid, const float* weights,
   ctx->launches = 5 + 5 + 1 + (cw->w.umma2 ? 4 : 0);
   // the tensor-core path reports a bounded wait that gave up
   if (cw->w.umma2) return cnn_flag_status(ctx, cw, st);
+  return AD_OK;
+}
+
+ad_status ad_guess_time_conv(ad_ctx* ctx, const ad_grid* grid, int batch, int reps, void* stream, double* ms,
+                             int* tensor_cores) {
+  if (!ctx) return AD_ERR_ARG;
+  ad_status s = check_cnn_grid(ctx, grid);
+  if (s != AD_OK) return s;
+  if (batch < 1 || reps < 1) return fail(ctx, AD_ERR_ARG, "need batch >= 1 and reps >= 1");
+  CK(cudaSetDevice(ctx->device));
+  CnnWork* cw = nullptr;
+  if ((s = get_cnn(ctx, grid, batch, false, &cw)) != AD_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int X = (int)grid->n[0], Y = (int)grid->n[1], Z = (int)grid->n[2];
+  const size_t act = sizeof(__nv_bfloat16) * (size_t)X * Y * Z * 32 * batch;
+  // defined inputs: zero weights and activations (the timing does not depend on the values)
+  CK(cudaMemsetAsync(cw->w.master, 0, sizeof(float) * kCnnWeights, st));
+  CK(cudaMemsetAsync(cw->w.H1, 0, act, st));
+  CK(cnn_pack(cw->w, st));
+  bool tc = false;
+  CK(cnn_conv_layer(cw->w, X, Y, Z, batch, st, &tc));          // warm-up
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  cudaError_t e = cudaEventRecord(e0, st);
+  for (int i = 0; i < reps && e == cudaSuccess; ++i) e = cnn_conv_layer(cw->w, X, Y, Z, batch, st, nullptr);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "ad_guess_time_conv");
+  if (ms) *ms = (double)t / reps;
+  if (tensor_cores) *tensor_cores = tc ? 1 : 0;
+  ctx->launches = reps + 1;
+  if (tc) return cnn_flag_status(ctx, cw, st);
   return AD_OK;
 }
 

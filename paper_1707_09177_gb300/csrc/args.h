@@ -12,16 +12,20 @@ namespace gad {
 struct FftStage {
   int radix;        // 2, 3, 4, 8 or 16
   int ns;           // size of the sub-transforms already formed
-  int tw_step;      // twiddle-table stride per unit of r*k
+  int tw_off;       // this stage's block in the plan's twiddle table
   float rcp_lr;     // 1 / (L / radix)
   float rcp_ns;     // 1 / ns
 };
 
+// The twiddle table of a plan holds, stage after stage, the factors
+// exp(-2 pi i r k / (radix ns)) at tw_off + (r - 1) ns + k (r = 1 .. radix-1,
+// k = 0 .. ns-1): the butterflies of consecutive threads (consecutive k) read
+// consecutive entries. L - 1 entries in all.
 struct FftPlan {
   int L;            // complex length
   int nst;          // number of stages
   FftStage st[8];
-  const void* tw;   // table of exp(-2 pi i m / Ltab), m in [0, Ltab)
+  const void* tw;   // the plan's twiddle table (complex, the field's precision)
 };
 
 // Prologue (forward x pass) opcodes: compute the field to transform and the

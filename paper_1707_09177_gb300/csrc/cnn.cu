@@ -725,6 +725,22 @@ cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const
   return cudaGetLastError();
 }
 
+// One forward 32 -> 32 layer, H2 = ReLU(conv(H1, W2)), in the launch shape of
+// inference (the tensor-core path when the grid allows it); for timing.
+cudaError_t cnn_conv_layer(const CnnBuffers& w, int X, int Y, int Z, int B, cudaStream_t s, bool* tensor_cores) {
+  const bool tc = w.umma2 && conv_tc_shape_ok(X, Y, Z);
+  if (tensor_cores) *tensor_cores = tc;
+  if (tc) return conv_tc_forward(w.H1, w.umma2, w.H2, nullptr, X, Y, Z, B, 0, w.flag, w.wait_ns, s);
+  const int TX = cnn_tile(X);
+  const size_t sm = cnn_conv_smem(X);
+  if (sm > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_conv_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_conv_mma<<<dim3((unsigned)(X / TX) * Y * Z, B), TX, sm, s>>>(w.H1, w.frag2, w.H2, nullptr, X, Y, Z, TX, 0);
+  return cudaGetLastError();
+}
+
 cudaError_t cnn_pack(const CnnBuffers& w, cudaStream_t s) {
   const int n = TAPS * 2 * 4 * 32;
   k_pack_frag<<<(n + 255) / 256, 256, 0, s>>>(w.master + kW2, w.frag2, 0);

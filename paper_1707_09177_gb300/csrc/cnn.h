@@ -55,6 +55,8 @@ cudaError_t cnn_forward(const CnnBuffers& w, const float* ubar, float* u0, const
                         int B, double ascale, cudaStream_t s);
 cudaError_t cnn_backward(const CnnBuffers& w, const float* ubar, int X, int Y, int Z, int B, cudaStream_t s);
 cudaError_t cnn_adam(const CnnBuffers& w, int step, float lr, cudaStream_t s);
+// one forward 32 -> 32 layer H2 = ReLU(conv(H1, W2)) in inference's launch shape (timing)
+cudaError_t cnn_conv_layer(const CnnBuffers& w, int X, int Y, int Z, int B, cudaStream_t s, bool* tensor_cores);
 
 // 32 -> 32 layers on the tcgen05 tensor cores (conv_tc.cu): grids whose x side
 // is a multiple of 128; others use the warp-level kernels of cnn.cu.

@@ -229,10 +229,12 @@ __device__ __forceinline__ void stage_io(int L, const FftStage& sg, const C* __r
       if constexpr (NSC > 0) k = (int)((unsigned)j % (unsigned)NSC);
       else k = j - ns * fquot(j, sg.rcp_ns);
       if (ns > 1) {
-        const int kt = k * sg.tw_step;
+        // factor r of butterfly k at tw_off + (r - 1) ns + k: consecutive
+        // threads read consecutive entries
+        const C* __restrict__ twk = tw + sg.tw_off + k;
 #pragma unroll
         for (int r = 1; r < R; ++r) {
-          const C w = tw[r * kt];
+          const C w = twk[(r - 1) * ns];
           v[b][r] = INV ? cmulc(v[b][r], w) : cmul(v[b][r], w);
         }
       }
@@ -304,9 +306,9 @@ __device__ __forceinline__ void stage_filter(int L, const FftStage& sg, const C*
     for (int b = 0; b < NB; ++b) {
       const int j = jj[b];                  // k = j: ns = L/R exceeds every j
       if (lr > 1) {
-        const int kt = j * sg.tw_step;
+        const C* __restrict__ twk = tw + sg.tw_off + j;     // ns = L/R = lr for the last stage
 #pragma unroll
-        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], tw[r * kt]);
+        for (int r = 1; r < R; ++r) v[b][r] = cmul(v[b][r], twk[(r - 1) * lr]);
       }
       dft<R, false>(v[b]);
 #pragma unroll
@@ -405,6 +407,7 @@ template <typename C, int E, class Load, class Mul, class Emit>
 __device__ __forceinline__ void fft_filter_run(C* s, int ld, const FftPlan& fwd, const FftPlan& inv, int tid, int nthr,
                                                Load& load, Mul& mul, Emit& emit) {
   const C* tw = reinterpret_cast<const C*>(fwd.tw);
+  const C* twi = reinterpret_cast<const C*>(inv.tw);
   SmemRows<C> rows{s, ld};
   const int n = fwd.nst;
   if (n == 1) {
@@ -419,11 +422,11 @@ __device__ __forceinline__ void fft_filter_run(C* s, int ld, const FftPlan& fwd,
   const FftStage sf = stage_at(fwd, n - 1);
   filter_dispatch<C, E>(fwd.L, sf, tw, tid, nthr, rows, mul, rows, true);
   __syncthreads();
-  if (n > 2) { stage_dispatch<C, E, true>(inv.L, inv.st[1], tw, tid, nthr, rows, rows, true); __syncthreads(); }
-  if (n > 3) { stage_dispatch<C, E, true>(inv.L, inv.st[2], tw, tid, nthr, rows, rows, true); __syncthreads(); }
-  if (n > 4) { stage_dispatch<C, E, true>(inv.L, inv.st[3], tw, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 2) { stage_dispatch<C, E, true>(inv.L, inv.st[1], twi, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 3) { stage_dispatch<C, E, true>(inv.L, inv.st[2], twi, tid, nthr, rows, rows, true); __syncthreads(); }
+  if (n > 4) { stage_dispatch<C, E, true>(inv.L, inv.st[3], twi, tid, nthr, rows, rows, true); __syncthreads(); }
   const FftStage sl = stage_at(inv, n - 1);
-  stage_dispatch<C, E, true>(inv.L, sl, tw, tid, nthr, rows, emit, false);
+  stage_dispatch<C, E, true>(inv.L, sl, twi, tid, nthr, rows, emit, false);
 }
 
 // --- fixed plans -----------------------------------------------------------
@@ -515,6 +518,7 @@ __device__ __forceinline__ void fft_filter_run_ct(C* s, int ld, const FftPlan& f
   constexpr int n = P::n;
   constexpr int RF = P::rad(n - 1);
   const C* tw = reinterpret_cast<const C*>(fwd.tw);
+  const C* twi = reinterpret_cast<const C*>(inv.tw);
   SmemRows<C> rows{s, ld};
   if constexpr (n == 1) {
     stage_filter<C, E, RF, L / RF>(L, fwd.st[0], tw, tid, nthr, load, mul, emit, false);
@@ -526,10 +530,10 @@ __device__ __forceinline__ void fft_filter_run_ct(C* s, int ld, const FftPlan& f
     if constexpr (n > 4) { ct_stage<C, E, false, L, false, 3>(fwd, tw, tid, nthr, rows, rows, true); __syncthreads(); }
     stage_filter<C, E, RF, L / RF>(L, stage_at(fwd, n - 1), tw, tid, nthr, rows, mul, rows, true);
     __syncthreads();
-    if constexpr (n > 2) { ct_stage<C, E, true, L, true, 1>(inv, tw, tid, nthr, rows, rows, true); __syncthreads(); }
-    if constexpr (n > 3) { ct_stage<C, E, true, L, true, 2>(inv, tw, tid, nthr, rows, rows, true); __syncthreads(); }
-    if constexpr (n > 4) { ct_stage<C, E, true, L, true, 3>(inv, tw, tid, nthr, rows, rows, true); __syncthreads(); }
-    ct_stage<C, E, true, L, true, n - 1>(inv, tw, tid, nthr, rows, emit, false);
+    if constexpr (n > 2) { ct_stage<C, E, true, L, true, 1>(inv, twi, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 3) { ct_stage<C, E, true, L, true, 2>(inv, twi, tid, nthr, rows, rows, true); __syncthreads(); }
+    if constexpr (n > 4) { ct_stage<C, E, true, L, true, 3>(inv, twi, tid, nthr, rows, rows, true); __syncthreads(); }
+    ct_stage<C, E, true, L, true, n - 1>(inv, twi, tid, nthr, rows, emit, false);
   }
 }
 

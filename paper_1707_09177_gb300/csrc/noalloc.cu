@@ -72,6 +72,34 @@ __global__ void k_static_twiddles(C* tw, int L) {
   tw[m] = C{(R)cs, (R)(-sn)};
 }
 
+// The twiddle table of an FFT plan (see FftPlan): entry e of stage q,
+// e = tw_off(q) + (r - 1) ns(q) + k, is exp(-2 pi i r k / (rad[q] ns(q))).
+struct RadixList {
+  int r[kMaxStages];
+  int n;
+};
+
+template <typename C, typename R>
+__global__ void k_static_plan_twiddles(C* tw, RadixList rl, int L) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= L - 1) return;
+  int ns = 1, off = 0;
+  for (int q = 0; q < rl.n; ++q) {
+    const int cnt = (rl.r[q] - 1) * ns;
+    if (e < off + cnt) {
+      const int r = (e - off) / ns + 1, k = (e - off) - (r - 1) * ns;
+      const int len = rl.r[q] * ns;
+      const long long m = ((long long)r * k) % len;
+      double sn, cs;
+      sincospi(2.0 * (double)m / (double)len, &sn, &cs);
+      tw[e] = C{(R)cs, (R)(-sn)};
+      return;
+    }
+    off += cnt;
+    ns *= rl.r[q];
+  }
+}
+
 struct StaticPass {
   TileShape t;
   FftPlan fft{}, fft_inv{};
@@ -81,12 +109,21 @@ struct StaticPass {
 
 // The same plan and tile shape as the context-owning entry points build
 // (plan.h), so the pass kernels take the same code paths.
-bool plan_s(int L, int slots, int div, size_t cs, const void* tab, long long Ltab, bool with_inverse,
-            StaticPass& pc) {
+bool plan_s(int L, int slots, int div, size_t cs, const void* tab, const void* tab_inv, StaticPass& pc) {
   const int E = pick_E(L);
-  if (!make_fft(L, E, tab, Ltab, pc.fft)) return false;
-  if (with_inverse && !make_fft(L, E, tab, Ltab, pc.fft_inv, true)) return false;
+  if (!make_fft(L, E, tab, pc.fft)) return false;
+  if (tab_inv && !make_fft(L, E, tab_inv, pc.fft_inv, true)) return false;
   return choose_tile(L, E, slots, div, cs, pc.t);
+}
+
+// Fills a plan's twiddle table on the device (stream order).
+template <typename C, typename R>
+bool plan_table_s(int L, bool reversed, C* tw, cudaStream_t st) {
+  RadixList rl{};
+  rl.n = plan_radices(L, pick_E(L), reversed, rl.r);
+  if (rl.n == 0) return false;
+  if (L > 1) k_static_plan_twiddles<C, R><<<(L - 1 + 255) / 256, 256, 0, st>>>(tw, rl, L);
+  return true;
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
@@ -98,27 +135,32 @@ ad_status run_static(const ad_grid* g, const void* in, void* out, int batch, cud
   const int kxn = nx / 2 + 1, M = nx / 2;
   const long long P = (long long)nx * ny * nz, SP = (long long)kxn * ny * nz;
   const size_t cs = sizeof(C);
-  // scratch layout: twiddles for x, y, z | S1 | S2 (3D)
-  const size_t tx = align256((size_t)nx * cs), ty = align256((size_t)ny * cs);
-  const size_t tz = g->ndim == 3 ? align256((size_t)nz * cs) : 0;
+  // scratch layout: the x split's table (nx) | the plans' twiddle tables (x
+  // plan: nx/2, filter plan and its reverse: L each, L the last axis; 3D: y
+  // plan, ny) | S1 | S2 (3D)
+  const int Lf = g->ndim == 3 ? nz : ny;
+  const size_t tx = align256((size_t)nx * cs), tpx = align256((size_t)M * cs), tpf = align256((size_t)Lf * cs);
+  const size_t tpy = g->ndim == 3 ? align256((size_t)ny * cs) : 0;
   const size_t sb = align256((size_t)SP * batch * cs);
-  const size_t need = tx + ty + tz + sb * (g->ndim == 3 ? 2 : 1);
+  const size_t tabs = tx + tpx + 2 * tpf + tpy;
+  const size_t need = tabs + sb * (g->ndim == 3 ? 2 : 1);
   if (need > (size_t)AD_STATIC_SCRATCH_BYTES) return AD_ERR_ARG;
   void* base = nullptr;
   if (scratch_address(&base) != cudaSuccess) return AD_ERR_CUDA;
   unsigned char* b = static_cast<unsigned char*>(base);
   C* twx = reinterpret_cast<C*>(b);
-  C* twy = reinterpret_cast<C*>(b + tx);
-  C* twz = reinterpret_cast<C*>(b + tx + ty);
-  void* S1 = b + tx + ty + tz;
-  void* S2 = g->ndim == 3 ? (void*)(b + tx + ty + tz + sb) : nullptr;
+  C* tpx_d = reinterpret_cast<C*>(b + tx);
+  C* tpf_d = reinterpret_cast<C*>(b + tx + tpx);
+  C* tpfi_d = reinterpret_cast<C*>(b + tx + tpx + tpf);
+  C* tpy_d = reinterpret_cast<C*>(b + tx + tpx + 2 * tpf);
+  void* S1 = b + tabs;
+  void* S2 = g->ndim == 3 ? (void*)(b + tabs + sb) : nullptr;
 
   StaticPass xf, fl, yf;
-  const int Lf = g->ndim == 3 ? nz : ny;
   const int nseq = g->ndim == 3 ? kxn * ny : kxn;
-  bool ok = plan_s(M, M + 1, pow2_part(ny), cs, twx, nx, false, xf);
-  ok = ok && plan_s(Lf, Lf, 0, cs, g->ndim == 3 ? (const void*)twz : (const void*)twy, Lf, true, fl);
-  if (g->ndim == 3) ok = ok && plan_s(ny, ny, pow2_part(nz), cs, twy, ny, false, yf);
+  bool ok = plan_s(M, M + 1, pow2_part(ny), cs, tpx_d, nullptr, xf);
+  ok = ok && plan_s(Lf, Lf, 0, cs, tpf_d, tpfi_d, fl);
+  if (g->ndim == 3) ok = ok && plan_s(ny, ny, pow2_part(nz), cs, tpy_d, nullptr, yf);
   if (!ok) return AD_ERR_ARG;
   xf.rcp_a = 1.0f / (float)(nx / 4);
   xf.rcp_b = 1.0f / (float)(M / 2 + 1);
@@ -127,8 +169,9 @@ ad_status run_static(const ad_grid* g, const void* in, void* out, int batch, cud
   if (g->ndim == 3) yf.grid = dim3(kxn * (nz / yf.t.W), batch);
 
   k_static_twiddles<C, T><<<(nx + 255) / 256, 256, 0, st>>>(twx, nx);
-  k_static_twiddles<C, T><<<(ny + 255) / 256, 256, 0, st>>>(twy, ny);
-  if (g->ndim == 3) k_static_twiddles<C, T><<<(nz + 255) / 256, 256, 0, st>>>(twz, nz);
+  ok = plan_table_s<C, T>(M, false, tpx_d, st) && plan_table_s<C, T>(Lf, false, tpf_d, st) &&
+       plan_table_s<C, T>(Lf, true, tpfi_d, st) && (g->ndim != 3 || plan_table_s<C, T>(ny, false, tpy_d, st));
+  if (!ok) return AD_ERR_ARG;
   if (cudaGetLastError() != cudaSuccess) return AD_ERR_CUDA;
 
   PassArgs<T> a{};

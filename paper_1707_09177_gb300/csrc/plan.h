@@ -58,41 +58,79 @@ inline int radices_for(int L, int E, int* rad) {
   return k;
 }
 
-// Stockham stage table for the radices rad[0..nrad) (in that order) over a
-// twiddle table of exp(-2 pi i m / Ltab), Ltab a multiple of L.
-inline bool make_fft_from(int L, const int* rad, int nrad, const void* tab, long long Ltab, FftPlan& fp) {
+// Stockham stage table for the radices rad[0..nrad) (in that order) over the
+// plan's twiddle table `tab` (see FftPlan; fill it with plan_twiddles).
+inline bool make_fft_from(int L, const int* rad, int nrad, const void* tab, FftPlan& fp) {
   if (nrad < 1 || nrad > kMaxStages) return false;
   fp = FftPlan{};
   fp.L = L;
   fp.nst = nrad;
   fp.tw = tab;
-  long long ns = 1;
+  long long ns = 1, off = 0;
   for (int q = 0; q < nrad; ++q) {
     FftStage& s = fp.st[q];
     s.radix = rad[q];
     s.ns = (int)ns;
-    s.tw_step = (int)(Ltab / (ns * rad[q]));
+    s.tw_off = (int)off;
     s.rcp_lr = 1.0f / (float)(L / rad[q]);
     s.rcp_ns = 1.0f / (float)ns;
+    off += (long long)(rad[q] - 1) * ns;
     ns *= rad[q];
   }
   return ns == L;
 }
 
-// The plan of length L for E elements per thread; `reversed` gives the same
-// radices in reverse order (the filter pass's inverse transform, whose first
-// stage meets the forward transform's last stage in registers).
-inline bool make_fft(int L, int E, const void* tab, long long Ltab, FftPlan& fp, bool reversed = false) {
-  int rad[kMaxStages];
+// Radices of the plan of length L for E elements per thread; `reversed` gives
+// them in reverse order (the filter pass's inverse transform, whose first
+// stage meets the forward transform's last stage in registers). Returns the
+// number of stages, 0 when there is no plan.
+inline int plan_radices(int L, int E, bool reversed, int* rad) {
   const int n = radices_for(L, E, rad);
-  if (n == 0) return false;
   if (reversed)
     for (int i = 0; i < n / 2; ++i) {
       const int t = rad[i];
       rad[i] = rad[n - 1 - i];
       rad[n - 1 - i] = t;
     }
-  return make_fft_from(L, rad, n, tab, Ltab, fp);
+  return n;
+}
+
+inline bool make_fft(int L, int E, const void* tab, FftPlan& fp, bool reversed = false) {
+  int rad[kMaxStages];
+  const int n = plan_radices(L, E, reversed, rad);
+  return n > 0 && make_fft_from(L, rad, n, tab, fp);
+}
+
+// The plan's twiddle table (L - 1 complex entries, interleaved re, im) in
+// long double, rounded to T: stage q, factor r, butterfly k at
+// tw_off(q) + (r - 1) ns(q) + k holds exp(-2 pi i r k / (rad[q] ns(q))); the
+// quarter and half turns are exact.
+template <typename T>
+inline void plan_twiddles(const int* rad, int nrad, T* out) {
+  const long double two_pi = 6.283185307179586476925286766559005768L;
+  long long ns = 1, off = 0;
+  for (int q = 0; q < nrad; ++q) {
+    const long long len = (long long)rad[q] * ns;
+    for (int r = 1; r < rad[q]; ++r)
+      for (long long k = 0; k < ns; ++k) {
+        const long long m = ((long long)r * k) % len;
+        long double c, sn;
+        if (m == 0) { c = 1; sn = 0; }
+        else if (4 * m == len) { c = 0; sn = -1; }
+        else if (2 * m == len) { c = -1; sn = 0; }
+        else if (4 * m == 3 * len) { c = 0; sn = 1; }
+        else {
+          const long double ang = two_pi * (long double)m / (long double)len;
+          c = cosl(ang);
+          sn = -sinl(ang);
+        }
+        const long long e = off + (long long)(r - 1) * ns + k;
+        out[2 * e] = (T)c;
+        out[2 * e + 1] = (T)sn;
+      }
+    off += (long long)(rad[q] - 1) * ns;
+    ns *= rad[q];
+  }
 }
 
 // Odd shared-memory row stride (complex units) of a tile row of `slots`
