@@ -292,10 +292,21 @@ def _uneven_48(gad, dev, out):
         ub.append(gad.filter(fields.random_scalar_field_torch(sh, 1000 + i, spec, device=dev), g, ndim=len(sh)))
         gammas.append(g)
     pts = float(sum(np.prod(sh) for sh in shapes))
+    # one graph branch per shape group (the default) ...
+    gad.set_batched_launch(False)
     res, t = _timed(lambda: gad.deconvolve_batched(ub, gammas, method="bicgstab", tol=1e-6, maxit=3000,
                                                    history=False))
     its = res[1]
     launches = gad.last_launch_count()
+    # ... against one launch per pass stage over all shape groups (a work list)
+    gad.set_batched_launch(True)
+    try:
+        resw, t_wl = _timed(lambda: gad.deconvolve_batched(ub, gammas, method="bicgstab", tol=1e-6, maxit=3000,
+                                                           history=False))
+        launches_wl = gad.last_launch_count()
+    finally:
+        gad.set_batched_launch(False)
+    same = bool(all(np.array_equal(a.cpu().numpy(), b.cpu().numpy()) for a, b in zip(res[0], resw[0])))
     # the same fields, one shape group per call
     groups = {}
     for i, sh in enumerate(shapes):
@@ -310,6 +321,10 @@ def _uneven_48(gad, dev, out):
     out["uneven48_f32"] = {"mpoints_s": pts / t / 1e6, "ms": t * 1e3, "points": pts, "fields": len(shapes),
                            "shape_groups": len(groups), "iterations_mean": float(np.mean(its)),
                            "converged": bool(np.all(res[2] == gad.AD_OK)), "launches": launches,
+                           "launch": "one CUDA graph, one concurrent branch (with its own loop) per shape group",
+                           "work_list": {"launch": "one launch per pass stage over all shape groups",
+                                         "mpoints_s": pts / t_wl / 1e6, "ms": t_wl * 1e3,
+                                         "launches": launches_wl, "bitwise_equal": same},
                            "one_call_per_group_mpoints_s": pts / t_seq / 1e6}
 
 

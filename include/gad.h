@@ -368,6 +368,22 @@ ad_status ad_set_wait_limit(ad_ctx* ctx, uint64_t ns);
  * AD_ERR_ARG for a NULL context. */
 ad_status ad_set_graph_mode(ad_ctx* ctx, int enable);
 
+/* How ad_deconvolve_batched runs a batch of several shapes. 0 (default): one
+ * branch per shape group in the batch's graph, each with its own loop; the
+ * branches run concurrently and each group stops when its fields converge.
+ * 1: one launch per pass stage over the blocks of every shape group (a
+ * device work list of (group, field, tile) blocks; groups whose pass has
+ * another per-thread element count or block size get a launch of their
+ * own), one loop for the whole batch; used for float32 Van Cittert, SD, CG
+ * and BiCGSTAB in physical space, every other method or precision keeps the
+ * branches. The results are bitwise the same either way (each group's passes
+ * run in their own launch shape). Measured on the 48-field uneven batch the
+ * branches are faster (the work list runs every stage until the slowest
+ * field converges). Cached batched graphs are dropped. Returns AD_ERR_ARG for
+ * a NULL context. No counterpart in the paper (Algorithms 1-4 solve one
+ * field). */
+ad_status ad_set_batched_launch(ad_ctx* ctx, int one_launch_per_stage);
+
 /* Number of kernel launches the last ad_filter / ad_deconvolve call issued
  * (graph-internal launches counted per executed kernel node). Library
  * housekeeping, no counterpart in the paper. */

@@ -46,7 +46,7 @@ EXPORTED = ("ad_create", "ad_destroy", "ad_filter", "ad_deconvolve", "ad_deconvo
             "ad_autotune", "ad_set_graph_mode", "ad_last_launch_count", "ad_status_str", "ad_last_error",
             "ad_filter_static", "ad_guess_weight_count", "ad_guess_init", "ad_guess_infer", "ad_guess_grad",
             "ad_guess_train", "ad_closure", "ad_spectrum", "ad_histogram", "ad_curl", "ad_set_wait_limit",
-            "ad_deconvolve_host", "ad_guess_time_conv")
+            "ad_deconvolve_host", "ad_guess_time_conv", "ad_set_batched_launch")
 PASS_KINDS = {0: "xfwd", 1: "xinv", 2: "filt", 3: "yfwd", 4: "yinv", 5: "lfwd", 6: "linv", 7: "spec", 8: "sten"}
 
 
@@ -113,6 +113,8 @@ def load(path=None):
     lib.ad_time_pass.restype = c_i
     lib.ad_set_graph_mode.argtypes = [c_p, c_i]
     lib.ad_set_graph_mode.restype = c_i
+    lib.ad_set_batched_launch.argtypes = [c_p, c_i]
+    lib.ad_set_batched_launch.restype = c_i
     lib.ad_last_launch_count.argtypes = [c_p]
     lib.ad_last_launch_count.restype = ctypes.c_int64
     lib.ad_status_str.argtypes = [c_i]
@@ -151,6 +153,13 @@ def context(device=None):
 
 def set_graph_mode(enable, device=None):
     load().ad_set_graph_mode(context(device), 1 if enable else 0)
+
+
+def set_batched_launch(one_launch_per_stage, device=None):
+    """Batched solves of several shapes: one graph branch per shape group
+    (False, default) or one launch per pass stage over every group (True)."""
+    ctx = context(device)
+    _check(load().ad_set_batched_launch(ctx, 1 if one_launch_per_stage else 0), ctx)
 
 
 def set_wait_limit(ns, device=None):

@@ -1,8 +1,8 @@
 """Builds the CUDA library libgad.so in-tree for sm_103a with nvcc.
 
 The translation units (host driver, float32 and float64 pass kernels, the
-allocation-free filter, the learned guess's warp-level and tcgen05 kernels)
-compile in parallel; the result is linked into
+multi-group pass kernels of batched solves, the allocation-free filter, the
+learned guess's warp-level and tcgen05 kernels) compile in parallel; the result is linked into
 paper_1707_09177_gb300/libgad.so next to this file.
 """
 
@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgad.so")
-SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "cnn.cu", "conv_tc.cu"]
+SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "kernels_multi.cu", "noalloc.cu", "cnn.cu", "conv_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

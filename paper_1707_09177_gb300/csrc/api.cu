@@ -94,6 +94,11 @@ struct BatchedEntry {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<BatchedGroup> groups;
+  // one launch per pass stage over all groups (k_multi): launches of the
+  // initial residual, of one loop body and of the finish; owned device arrays
+  bool multi = false;
+  int m_init = 0, m_body = 0, m_fin = 0;
+  std::vector<void*> owned;
 };
 
 struct CnnWork {
@@ -109,6 +114,7 @@ struct CnnWork {
 struct ad_ctx {
   std::map<std::string, CnnWork*> cnn;        // learned-guess workspaces by (shape, batch)
   bool autotune = false;                      // tune the tiles of every new plan of a batched solve
+  bool batched_multi = false;                 // batched solves: one launch per pass stage over all groups
   std::vector<LaunchRec>* record = nullptr;   // when set, pass launches are recorded, not issued
   std::map<std::string, BatchedEntry> bgraphs;
   std::vector<cudaStream_t> branches;         // capture streams of the batched graph's branches
@@ -428,6 +434,7 @@ void drop_graphs(ad_ctx* ctx) {
   for (auto& kv : ctx->bgraphs) {
     if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
     if (kv.second.g) cudaGraphDestroy(kv.second.g);
+    for (void* q : kv.second.owned) cudaFree(q);
   }
   ctx->bgraphs.clear();
 }
@@ -690,11 +697,11 @@ ad_status enqueue_spec_body(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO&
   }
 }
 
+// The initial residual r0 = u_bar - G u0 (and, with an explicit u0, the
+// reference ||u_bar - G u_bar||): the passes of the physical-space init,
+// after the state reset.
 template <typename T>
-ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
-  if (io.spectral) return enqueue_spec_init<T>(ctx, p, s, io, c, nl);
-  CK(launch_reset_state(p->st, p->batch, s));
-  ++*nl;
+ad_status enqueue_init_passes(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
   ad_status r;
   if (io.u0) {
     Fwd fw; fw.op = XF_COPY; fw.A = io.ubar;
@@ -705,6 +712,14 @@ ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, 
   Inv iv; iv.op = XI_INIT; iv.A = io.ubar; iv.O1 = p->R; iv.O2 = io.method == AD_BICGSTAB ? p->F0 : nullptr;
   iv.ndots = 1; iv.stage = SS_INIT;
   return enqueue_G<T>(ctx, p, s, fw, Flt{}, iv, c, nl);
+}
+
+template <typename T>
+ad_status enqueue_init(ad_ctx* ctx, Plan* p, cudaStream_t s, const SolveIO& io, const Common& c, int* nl) {
+  if (io.spectral) return enqueue_spec_init<T>(ctx, p, s, io, c, nl);
+  CK(launch_reset_state(p->st, p->batch, s));
+  ++*nl;
+  return enqueue_init_passes<T>(ctx, p, s, io, c, nl);
 }
 
 // z = M r (the preconditioner stencil) with the dot (r, z) -> rho, beta.
@@ -1222,8 +1237,253 @@ ad_status capture_group(ad_ctx* ctx, BatchedGroup& gr, cudaStream_t s, cudaGraph
   return AD_OK;
 }
 
+// --- one launch per pass stage over all shape groups -----------------------
+// The groups' own pass launches (recorded, not issued) are lined up by stage
+// -- the k-th application of G in the sequence, and within it the x, y,
+// filter, inverse y and inverse x passes -- and each stage becomes one k_multi
+// launch per per-thread element count E over every group's blocks: a device
+// work list of (group, field, tile) blocks; groups whose passes have other
+// block sizes go to a launch of their own. 2D groups take no part in the y
+// stages. The fields' dot reductions and scalar recurrences stay per group;
+// the count of finished fields and the loop condition span all groups
+// (MultiState).
+
+int stage_slot(int kind) {
+  switch (kind) {
+    case PK_XFWD: return 0;
+    case PK_YFWD: return 1;
+    case PK_FILT: return 2;
+    case PK_YINV: return 3;
+    default: return 4;                 // PK_XINV
+  }
+}
+
+struct MultiLaunch {
+  int kind = 0, E = 0, blocks = 0, threads = 0, ngroups = 0;
+  size_t smem = 0;
+  const void* args = nullptr;          // device PassArgs<float>[ngroups]
+  const int* start = nullptr;          // device int[ngroups + 1]
+};
+
+// Lines the groups' recorded launches up by stage and uploads one launch per
+// (stage, E, block size). `first_clear`: only the first launch's first group keeps the
+// loop-condition reset of the body's first pass.
+ad_status merge_multi(ad_ctx* ctx, BatchedEntry& be, std::vector<std::vector<LaunchRec>>& recs, MultiState* ms,
+                      bool first_clear, std::vector<MultiLaunch>& out) {
+  // stage index of every record: 5 * (application of G) + slot of the pass
+  // stage -> (E, block size) -> records: the groups of one launch share the
+  // block size too, so every thread does the same work as in the group's own
+  // launch and the reductions round identically
+  std::map<int, std::map<std::pair<int, int>, std::vector<const LaunchRec*>>> stages;
+  for (auto& rl : recs) {
+    int app = -1;
+    for (const LaunchRec& r : rl) {
+      if (r.kind == PK_XFWD) ++app;
+      if (r.f64 || r.kind > PK_YINV || app < 0) return fail(ctx, AD_ERR_ARG, "no multi-group launch for this pass");
+      stages[5 * app + stage_slot(r.kind)][std::make_pair(r.E, r.threads)].push_back(&r);
+    }
+  }
+  bool cleared = false;
+  for (auto& st : stages) {
+    for (auto& byE : st.second) {
+      const auto& rs = byE.second;
+      MultiLaunch m;
+      m.kind = rs[0]->kind;
+      m.E = byE.first.first;
+      m.ngroups = (int)rs.size();
+      std::vector<PassArgs<float>> args(rs.size());
+      std::vector<int> start(rs.size() + 1, 0);
+      for (size_t g = 0; g < rs.size(); ++g) {
+        PassArgs<float> a = rs[g]->af;
+        a.vgx = (int)rs[g]->grid.x;
+        a.vgy = (int)rs[g]->grid.y;
+        a.vbd = rs[g]->threads;
+        a.ms = ms;
+        if (a.clear_cond) {
+          a.clear_cond = (first_clear && !cleared) ? 1 : 0;
+          cleared = true;
+        }
+        args[g] = a;
+        start[g + 1] = start[g] + (int)(rs[g]->grid.x * rs[g]->grid.y);
+        m.threads = std::max(m.threads, rs[g]->threads);
+        m.smem = std::max(m.smem, rs[g]->smem);
+      }
+      m.blocks = start.back();
+      void *da = nullptr, *ds = nullptr;
+      if (cudaMalloc(&da, sizeof(PassArgs<float>) * args.size()) != cudaSuccess ||
+          cudaMalloc(&ds, sizeof(int) * start.size()) != cudaSuccess) {
+        cudaGetLastError();
+        if (da) cudaFree(da);
+        return fail(ctx, AD_ERR_NOMEM, "multi-group launch arrays");
+      }
+      be.owned.push_back(da);
+      be.owned.push_back(ds);
+      CK(cudaMemcpy(da, args.data(), sizeof(PassArgs<float>) * args.size(), cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(ds, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+      m.args = da;
+      m.start = (const int*)ds;
+      out.push_back(m);
+    }
+  }
+  return AD_OK;
+}
+
+cudaError_t issue_multi(const std::vector<MultiLaunch>& ml, cudaStream_t s) {
+  for (const MultiLaunch& m : ml) {
+    const cudaError_t e = launch_multi<float>(m.kind, m.E, m.blocks, m.threads, m.smem, s,
+                                              static_cast<const PassArgs<float>*>(m.args), m.start, m.ngroups);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Float32 physical-space Van Cittert, SD, CG and BiCGSTAB without a
+// preconditioner (the other variants keep one graph branch per group).
+bool multi_eligible(const BatchedEntry& be, int method) {
+  if (method_spectral(method) || method_precond(method) || be.groups.size() < 2) return false;
+  for (const BatchedGroup& gr : be.groups)
+    if (gr.p->f64) return false;
+  return true;
+}
+
+ad_status build_batched_multi(ad_ctx* ctx, BatchedEntry& be, const void* const* ubar, void* const* u_out, int method,
+                              double tol, int maxit) {
+  const size_t G = be.groups.size();
+  // MultiState: counters, and every group's field states
+  MultiState hms{};
+  hms.ngroups = (int)G;
+  std::vector<FieldState*> sts(G);
+  std::vector<int> cnt(G);
+  for (size_t j = 0; j < G; ++j) {
+    sts[j] = be.groups[j].p->st;
+    cnt[j] = (int)be.groups[j].fields.size();
+    hms.nfields += cnt[j];
+  }
+  void *dms = nullptr, *dst = nullptr, *dcnt = nullptr;
+  if (cudaMalloc(&dms, sizeof(MultiState)) != cudaSuccess || cudaMalloc(&dst, sizeof(FieldState*) * G) != cudaSuccess ||
+      cudaMalloc(&dcnt, sizeof(int) * G) != cudaSuccess) {
+    cudaGetLastError();
+    if (dms) cudaFree(dms);
+    if (dst) cudaFree(dst);
+    return fail(ctx, AD_ERR_NOMEM, "multi-group state");
+  }
+  be.owned.push_back(dms);
+  be.owned.push_back(dst);
+  be.owned.push_back(dcnt);
+  hms.st = (FieldState**)dst;
+  hms.count = (int*)dcnt;
+  CK(cudaMemcpy(dst, sts.data(), sizeof(FieldState*) * G, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dcnt, cnt.data(), sizeof(int) * G, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(dms, &hms, sizeof(MultiState), cudaMemcpyHostToDevice));
+  MultiState* ms = (MultiState*)dms;
+
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle h;
+  cudaError_t e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaGraphConditionalHandleCreate"); }
+  // record every group's init and body launches
+  std::vector<std::vector<LaunchRec>> rinit(G), rbody(G);
+  ad_status st = AD_OK;
+  for (size_t j = 0; j < G && st == AD_OK; ++j) {
+    Plan* p = be.groups[j].p;
+    Common c;
+    c.st = p->st;
+    c.wait_ns = ctx->wait_ns;
+    c.cfg.tol = tol;
+    c.cfg.maxit = maxit;
+    c.cfg.method = method_base(method);
+    c.cfg.hist = p->hist;
+    c.cfg.hist_ld = p->hist_cap;
+    c.cond = h;
+    c.in_graph = true;
+    SolveIO io{p->Bin, p->Bout, nullptr, method_base(method), false, false, false};
+    int n = 0;
+    ctx->record = &rinit[j];
+    st = enqueue_init_passes<float>(ctx, p, nullptr, io, c, &n);
+    if (st == AD_OK) {
+      ctx->record = &rbody[j];
+      st = enqueue_body<float>(ctx, p, nullptr, io, c, &n);
+    }
+    ctx->record = nullptr;
+  }
+  std::vector<MultiLaunch> minit, mbody;
+  if (st == AD_OK) st = merge_multi(ctx, be, rinit, ms, false, minit);
+  if (st == AD_OK) st = merge_multi(ctx, be, rbody, ms, true, mbody);
+  if (st != AD_OK) { cudaGraphDestroy(g); return st; }
+  e = cudaStreamBeginCaptureToGraph(ctx->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaStreamBeginCaptureToGraph"); }
+  // gather, reset the states, the initial residual of every field
+  for (size_t j = 0; j < G && st == AD_OK; ++j) {
+    const BatchedGroup& gr = be.groups[j];
+    const size_t bytes = (size_t)gr.p->P * sizeof(float);
+    for (size_t k = 0; k < gr.fields.size() && e == cudaSuccess; ++k)
+      e = cudaMemcpyAsync((char*)gr.p->Bin + k * bytes, ubar[gr.fields[k]], bytes, cudaMemcpyDeviceToDevice, ctx->cap);
+    if (e == cudaSuccess) e = launch_reset_state(gr.p->st, (int)gr.fields.size(), ctx->cap);
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "multi-group gather");
+  }
+  if (st == AD_OK && (e = issue_multi(minit, ctx->cap)) != cudaSuccess) st = cuda_fail(ctx, e, "multi-group init");
+  if (st == AD_OK) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t cg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    cudaGraphNode_t cn = nullptr;
+    cudaGraphNodeParams np{};
+    e = cudaStreamGetCaptureInfo(ctx->cap, &cs, nullptr, &cg, &deps, nullptr, &nd);
+    if (e == cudaSuccess) {
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      e = cudaGraphAddNode(&cn, cg, deps, nullptr, nd, &np);
+    }
+    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(ctx->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCaptureToGraph(ctx->cap2, np.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      const cudaError_t eb = issue_multi(mbody, ctx->cap2);
+      cudaGraph_t bg = nullptr;
+      e = cudaStreamEndCapture(ctx->cap2, &bg);
+      if (eb != cudaSuccess) e = eb;
+    }
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "multi-group loop body");
+  }
+  // finish (CG's deferred update) and scatter, per group
+  int nfin = 0;
+  for (size_t j = 0; j < G && st == AD_OK; ++j) {
+    const BatchedGroup& gr = be.groups[j];
+    Common c;
+    c.st = gr.p->st;
+    c.wait_ns = ctx->wait_ns;
+    SolveIO io{gr.p->Bin, gr.p->Bout, nullptr, method_base(method), false, false, false};
+    st = enqueue_finish<float>(ctx, gr.p, ctx->cap, io, c, &nfin);
+    const size_t bytes = (size_t)gr.p->P * sizeof(float);
+    for (size_t k = 0; k < gr.fields.size() && st == AD_OK; ++k)
+      if (cudaMemcpyAsync(u_out[gr.fields[k]], (char*)gr.p->Bout + k * bytes, bytes, cudaMemcpyDeviceToDevice,
+                          ctx->cap) != cudaSuccess)
+        st = cuda_fail(ctx, cudaGetLastError(), "multi-group scatter");
+  }
+  cudaGraph_t gout = nullptr;
+  e = cudaStreamEndCapture(ctx->cap, &gout);
+  if (st == AD_OK && e != cudaSuccess) st = cuda_fail(ctx, e, "cudaStreamEndCapture(multi-group)");
+  if (st != AD_OK) { cudaGetLastError(); cudaGraphDestroy(g); return st; }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) { cudaGraphDestroy(g); return cuda_fail(ctx, e, "cudaGraphInstantiate(multi-group)"); }
+  be.g = g;
+  be.exec = exec;
+  be.multi = true;
+  be.m_init = (int)minit.size() + (int)G;
+  be.m_body = (int)mbody.size();
+  be.m_fin = nfin;
+  return AD_OK;
+}
+
 ad_status build_batched(ad_ctx* ctx, BatchedEntry& be, const void* const* ubar, void* const* u_out, int method,
                         double tol, int maxit) {
+  if (ctx->batched_multi && multi_eligible(be, method)) return build_batched_multi(ctx, be, ubar, u_out, method, tol, maxit);
   const size_t G = be.groups.size();
   ad_status st = ensure_streams(ctx, G);
   if (st != AD_OK) return st;
@@ -1463,6 +1723,7 @@ ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, 
   CK(cudaStreamSynchronize(st));
   ad_status worst = AD_OK;
   int64_t launches = 0;
+  int maxpass_all = 0;
   for (size_t j = 0; j < it->second.groups.size(); ++j) {
     const BatchedGroup& gr = it->second.groups[j];
     int maxpass = 0;
@@ -1475,7 +1736,10 @@ ad_status ad_deconvolve_batched(ad_ctx* ctx, int nfields, const ad_grid* grids, 
       maxpass = std::max(maxpass, f.iter + (f.status == AD_BREAKDOWN ? 1 : 0));
     }
     launches += gr.n_init + gr.n_fin + (int64_t)std::max(1, maxpass) * gr.n_body;
+    maxpass_all = std::max(maxpass_all, maxpass);
   }
+  if (it->second.multi)
+    launches = it->second.m_init + it->second.m_fin + (int64_t)std::max(1, maxpass_all) * it->second.m_body;
   ctx->launches = launches;
   return worst;
 }
@@ -1675,6 +1939,18 @@ ad_status ad_guess_train(ad_ctx* ctx, const ad_grid* grid, int npairs, const flo
 ad_status ad_set_graph_mode(ad_ctx* c, int enable) {
   if (!c) return AD_ERR_ARG;
   c->use_graph = enable != 0;
+  return AD_OK;
+}
+
+ad_status ad_set_batched_launch(ad_ctx* ctx, int one_launch_per_stage) {
+  if (!ctx) return AD_ERR_ARG;
+  const bool m = one_launch_per_stage != 0;
+  if (m != ctx->batched_multi) {
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaDeviceSynchronize());
+    drop_graphs(ctx);
+  }
+  ctx->batched_multi = m;
   return AD_OK;
 }
 

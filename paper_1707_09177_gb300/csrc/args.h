@@ -79,6 +79,17 @@ enum SpOp : int {
   SP_PCG = 12,    // preconditioned CG: O1 += alpha A; O2 -= alpha G A; d = (O2, O2), (O2, M O2)
 };
 
+// A batched solve whose passes serve several shape groups per launch: the
+// count of fields done in the current pass and the loop passes ([0], [1]),
+// and every group's field states for the loop condition.
+struct MultiState {
+  unsigned ticket[4];
+  int ngroups;
+  int nfields;               // fields of all groups
+  FieldState** st;           // [ngroups] the group's field states
+  int* count;                // [ngroups] the group's field count
+};
+
 template <typename T>
 struct PassArgs {
   int nx, ny, nz, kxn;       // real grid and kxn = nx/2 + 1
@@ -101,6 +112,9 @@ struct PassArgs {
   unsigned long long wait_ns;  // limit of a bounded device wait (0: give up at once)
   int chunk;                 // preconditioner stencil: positions of the march axis per block
   int rev;                   // fields in reverse launch order: field f = gridDim.y - 1 - blockIdx.y
+  int vgx, vgy;              // launch shape of this group's pass (blocks per field, fields) in k_multi
+  int vbd;                   // block size of that launch shape (0: blockDim.x)
+  MultiState* ms;            // nullptr, or the batched solve this pass belongs to (k_multi)
   void* S1;
   void* S2;
   const T* A;

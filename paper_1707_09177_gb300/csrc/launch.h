@@ -22,6 +22,13 @@ template <typename T>
 cudaError_t launch_pass(int kind, int E, dim3 grid, int threads, size_t smem, cudaStream_t s,
                         const PassArgs<T>& a);
 
+// One pass kind over several shape groups (k_multi): `args` (device) holds
+// each group's PassArgs (vgx, vgy its own launch shape), `start` (device,
+// ngroups + 1 entries) the first block of each group; blocks = start[ngroups].
+template <typename T>
+cudaError_t launch_multi(int kind, int E, int blocks, int threads, size_t smem, cudaStream_t s,
+                         const PassArgs<T>* args, const int* start, int ngroups);
+
 template <typename T>
 cudaError_t launch_cg_finish(T* u, const T* p, const FieldState* st, long long P, int batch, cudaStream_t s);
 

@@ -55,6 +55,20 @@ __device__ __forceinline__ int field_of(const A& a) {
   return a.rev ? (int)gridDim.y - 1 - (int)blockIdx.y : (int)blockIdx.y;
 }
 
+// Block coordinates of a pass: the launch's own (blockIdx, gridDim) when the
+// pass runs for one shape, or a block's place in its shape group's launch
+// shape when one launch serves several groups (k_multi).
+struct VBlock {
+  int x, y, nx, ny;
+};
+__device__ __forceinline__ VBlock own_block() {
+  return VBlock{(int)blockIdx.x, (int)blockIdx.y, (int)gridDim.x, (int)gridDim.y};
+}
+template <typename A>
+__device__ __forceinline__ int field_of(const A& a, const VBlock& vb) {
+  return a.rev ? vb.ny - 1 - vb.y : vb.y;
+}
+
 // G_hat(k) = k_c^2/(k_c^2 + |k|^2). float32: reciprocal-based quotient
 // (__fdividef, within 2 ulp; the spectra are stored in float32 anyway);
 // float64: IEEE division.
@@ -214,6 +228,31 @@ __device__ inline void scalar_update(int stage, FieldState& s, const double* d, 
   }
 }
 
+// A sum carried as an unevaluated pair of floats (hi + lo): TwoSum of the
+// high parts, the low parts and the rounding error added and the pair
+// renormalised. About twice float32 precision with float32 arithmetic: the
+// block reductions of the float32 dots use it instead of float64, whose rate
+// on this GPU is a small fraction of float32's.
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bp = s - a.x;
+  const float e = (a.x - (s - bp)) + (b.x - bp);
+  const float t = e + (a.y + b.y);
+  const float hi = s + t;
+  return make_float2(hi, t - (hi - s));
+}
+
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    float2 w;
+    w.x = __shfl_xor_sync(0xffffffffu, v.x, o);
+    w.y = __shfl_xor_sync(0xffffffffu, v.y, o);
+    v = pair_add(v, w);
+  }
+  return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -228,27 +267,55 @@ __device__ __forceinline__ double warp_sum(double v) {
 // the last one sets the graph's loop condition. ticket[1] counts loop passes
 // of the current solve (reset by the initial-residual pass).
 template <typename T>
-__device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, bool act) {
+__device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, bool act, const VBlock& vb) {
   __shared__ double red[32][3];
   __shared__ int last_field;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nw = (blockDim.x + 31) >> 5;
-  const int nblk = gridDim.x;
+  // the block size of the pass's own launch shape (a k_multi block may be
+  // larger: its extra threads hold no terms), so that the reduction order,
+  // and with it every rounding, is the same in both kinds of launch
+  const int nthr = a.vbd ? a.vbd : (int)blockDim.x;
+  const int nw = (nthr + 31) >> 5;
+  const int nblk = vb.nx;
   if (act) {
-    double v[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) v[d] = warp_sum(acc[d].value());
-    if (lane == 0) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) red[warp][d] = v[d];
-    }
-    __syncthreads();
-    if (warp == 0) {
+    if constexpr (sizeof(T) == 4) {
+      // float32 dots: the thread's compensated pair, reduced as float pairs
+      __shared__ float2 redf[32][3];
+      float2 v[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        double t = lane < nw ? red[lane][d] : 0.0;
-        t = warp_sum(t);
-        if (lane == 0) a.part[((long long)f * nblk + blockIdx.x) * 4 + d] = t * a.inv_p;
+        const float hi = acc[d].s + acc[d].c;
+        v[d] = warp_sum(make_float2(hi, acc[d].c - (hi - acc[d].s)));
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) redf[warp][d] = v[d];
+      }
+      __syncthreads();
+      if (warp == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          float2 t = lane < nw ? redf[lane][d] : make_float2(0.f, 0.f);
+          t = warp_sum(t);
+          if (lane == 0) a.part[((long long)f * nblk + vb.x) * 4 + d] = ((double)t.x + (double)t.y) * a.inv_p;
+        }
+      }
+    } else {
+      double v[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] = warp_sum(acc[d].value());
+      if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) red[warp][d] = v[d];
+      }
+      __syncthreads();
+      if (warp == 0) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          double t = lane < nw ? red[lane][d] : 0.0;
+          t = warp_sum(t);
+          if (lane == 0) a.part[((long long)f * nblk + vb.x) * 4 + d] = t * a.inv_p;
+        }
       }
     }
   }
@@ -264,7 +331,7 @@ __device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, boo
   if (act) {                    // act is the field's flag: every block of f saw the same value
     double t[3] = {0.0, 0.0, 0.0};
     const double* pf = a.part + (long long)f * nblk * 4;
-    for (int b = tid; b < nblk; b += blockDim.x) {
+    for (int b = tid; b < nblk && tid < nthr; b += nthr) {
 #pragma unroll
       for (int d = 0; d < 3; ++d) t[d] += __ldcg(pf + (long long)b * 4 + d);
     }
@@ -289,21 +356,37 @@ __device__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, boo
   if (tid == 0) {
     a.ticket[2 + f] = 0u;
     __threadfence();
-    const unsigned prevg = atomicAdd(a.ticket, 1u);
-    if (prevg == gridDim.y - 1u) {                        // every field is reduced
+    // fields done: those of this launch, or, when one sequence of launches
+    // serves several shape groups, those of every group (MultiState)
+    unsigned* done = a.ms ? a.ms->ticket : a.ticket;
+    const unsigned nfields = a.ms ? (unsigned)a.ms->nfields : (unsigned)vb.ny;
+    const unsigned prevg = atomicAdd(done, 1u);
+    if (prevg == nfields - 1u) {                          // every field is reduced
       __threadfence();
-      if (a.stage == SS_INIT || a.stage == SS_PCG_INIT) a.ticket[1] = 0u;
+      if (a.stage == SS_INIT || a.stage == SS_PCG_INIT) done[1] = 0u;
       if (a.set_cond) {
         unsigned any = 0;
-        for (int g = 0; g < a.batch; ++g) any |= (*(volatile const int*)&a.st[g].active != 0);
+        if (a.ms) {
+          for (int g = 0; g < a.ms->ngroups; ++g) {
+            const FieldState* sg = a.ms->st[g];
+            for (int k = 0; k < a.ms->count[g]; ++k) any |= (*(volatile const int*)&sg[k].active != 0);
+          }
+        } else {
+          for (int g = 0; g < a.batch; ++g) any |= (*(volatile const int*)&a.st[g].active != 0);
+        }
         // every field stops by maxit passes; never iterate past that bound
-        const unsigned loops = ++a.ticket[1];
+        const unsigned loops = ++done[1];
         if (loops > (unsigned)a.cfg.maxit + 1u) any = 0;
         cudaGraphSetConditional(a.cond, any);
       }
-      a.ticket[0] = 0u;
+      done[0] = 0u;
     }
   }
+}
+
+template <typename T>
+__device__ __forceinline__ void block_finish(const PassArgs<T>& a, const Acc<T>* acc, int f, bool act) {
+  block_finish(a, acc, f, act, own_block());
 }
 
 // ---------------------------------------------------------------------------
@@ -433,7 +516,7 @@ __device__ __forceinline__ void pair_offsets(const PassArgs<T>& a, int f, long l
 // the shared-memory rows as packed complex (z[n] = x[2n] + i x[2n+1]).
 template <typename T, int U>
 __device__ __forceinline__ void xfwd_prologue(const PassArgs<T>& a, typename cpx<T>::t* s, long long base, bool first,
-                                              T al, T be, T om, int tid, int nthr) {
+                                              T al, T be, T om, int tid, int nthr, int f) {
   const T* __restrict__ vA = a.A;
   const T* __restrict__ vB = a.B;
   T* __restrict__ vO1 = a.O1;
@@ -509,8 +592,8 @@ __device__ __forceinline__ void xfwd_prologue(const PassArgs<T>& a, typename cpx
     }
     case XF_MUL: {                                // closure: x = A_i A_j
       long long oi, oj;
-      pair_offsets(a, field_of(a), oi, oj);
-      const long long fb = (long long)field_of(a) * a.P;
+      pair_offsets(a, f, oi, oj);
+      const long long fb = (long long)f * a.P;
       auto ldf = [&](int u, long long g) { r_[u] = ld4(vA + (g - fb) + oi); y_[u] = ld4(vA + (g - fb) + oj); };
       auto fin = [&](int u, int w, int q, long long) {
         V4<T> xo;
@@ -538,7 +621,7 @@ __device__ __forceinline__ void xfwd_prologue(const PassArgs<T>& a, typename cpx
 // are streamed over the block's row tile.
 template <typename T, int U>
 __device__ __forceinline__ void xinv_epilogue(const PassArgs<T>& a, const typename cpx<T>::t* s, long long base, T al,
-                                              T om, Acc<T>& acc0, Acc<T>& acc1, int tid, int nthr) {
+                                              T om, Acc<T>& acc0, Acc<T>& acc1, int tid, int nthr, int f) {
   const T* __restrict__ vA = a.A;
   const T* __restrict__ vB = a.B;
   const T* __restrict__ vC = a.C;
@@ -638,8 +721,8 @@ __device__ __forceinline__ void xinv_epilogue(const PassArgs<T>& a, const typena
     }
     case XI_TAU: {                                // closure: O1 = B_i B_j - y
       long long oi, oj;
-      pair_offsets(a, field_of(a), oi, oj);
-      const long long fb = (long long)field_of(a) * a.P;
+      pair_offsets(a, f, oi, oj);
+      const long long fb = (long long)f * a.P;
       auto ldf = [&](int u, long long g) { b_[u] = ld4(vB + (g - fb) + oi); c_[u] = ld4(vB + (g - fb) + oj); };
       auto fin = [&](int u, int w, int q, long long g) {
         const V4<T> y = get_pair<T>(s + w * ld, q);
@@ -662,17 +745,17 @@ __device__ __forceinline__ void xinv_epilogue(const PassArgs<T>& a, const typena
 // split and the transposed store to S1.
 //   rcp_a = 1/(nx/4), rcp_b = 1/(nx/4 + 1)
 template <typename T, int E>
-__global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
+__device__ __forceinline__ void xfwd_body(const PassArgs<T>& a, const VBlock& vb) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = field_of(a);
-  if (a.clear_cond && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
+  const int f = field_of(a, vb);
+  if (a.clear_cond && vb.x == 0 && vb.y == 0 && threadIdx.x == 0) cudaGraphSetConditional(a.cond, 0u);
   FieldState* st = a.st ? a.st + f : nullptr;
   if (st && !st->active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nx = a.nx, M = nx >> 1;
-  const int row0 = blockIdx.x * a.W;
+  const int row0 = vb.x * a.W;
   const int z = row0 / a.ny, y0 = row0 - z * a.ny;
   const long long base = (long long)f * a.P + (long long)row0 * nx;
   const bool first = st ? (st->iter == 0) : true;
@@ -695,7 +778,7 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
     if ((op == XF_CG || op == XF_BI_P) && !first) prefetch_l2(a.O2 + base, tb, tid, nthr);
     if ((op == XF_BI_P && !first) || op == XF_BI_S) prefetch_l2(a.B + base, tb, tid, nthr);
   }
-  xfwd_prologue<T, 2>(a, s, base, first, al, be, om, tid, nthr);
+  xfwd_prologue<T, 2>(a, s, base, first, al, be, om, tid, nthr, f);
   __syncthreads();
   SmemRows<C> rows{s, a.ld};
   if (!fft_run_fixed<C, E, false, 1024>(s, a.ld, a.fft, tid, a.tfft, rows, rows, true, true) &&
@@ -727,21 +810,26 @@ __global__ void GAD_BOUNDS(T, E) k_xfwd(PassArgs<T> a) {
   store_transposed(s, a.ld, S1, a.ny, a.W, M + 1, tid, nthr);
 }
 
+template <typename T, int E>
+__global__ void GAD_BOUNDS(T, E) k_xfwd(const __grid_constant__ PassArgs<T> a) {
+  xfwd_body<T, E>(a, own_block());
+}
+
 // Inverse x pass: transposed load from S1, complex-to-real preparation, FFT
 // in shared memory, then the fused epilogue and dots streamed over the row
 // tile.
 template <typename T, int E>
-__global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
+__device__ __forceinline__ void xinv_body(const PassArgs<T>& a, const VBlock& vb) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = field_of(a);
+  const int f = field_of(a, vb);
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int nx = a.nx, M = nx >> 1;
-  const int row0 = blockIdx.x * a.W;
+  const int row0 = vb.x * a.W;
   const int z = row0 / a.ny, y0 = row0 - z * a.ny;
   Acc<T> acc[3];
   if (act) {
@@ -797,11 +885,16 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
     }
     const T al = st ? T(st->alpha) : T(0), om = st ? T(st->omega) : T(0);
     Acc<T> acc0, acc1;
-    xinv_epilogue<T, 2>(a, s, base, al, om, acc0, acc1, tid, nthr);
+    xinv_epilogue<T, 2>(a, s, base, al, om, acc0, acc1, tid, nthr, f);
     acc[0] = acc0;
     acc[1] = acc1;
   }
-  if (a.ndots) block_finish(a, acc, f, act);
+  if (a.ndots) block_finish(a, acc, f, act, vb);
+}
+
+template <typename T, int E>
+__global__ void GAD_BOUNDS(T, E) k_xinv(const __grid_constant__ PassArgs<T> a) {
+  xinv_body<T, E>(a, own_block());
 }
 
 // Filter pass along the last axis (y in 2D, z in 3D): forward FFT of W
@@ -810,11 +903,11 @@ __global__ void GAD_BOUNDS(T, E) k_xinv(PassArgs<T> a) {
 // back. fft holds the forward plan, fft_inv the reversed one. In 3D the
 // sequence index is kx*ny + ky.
 template <typename T, int E>
-__global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
+__device__ __forceinline__ void filt_body(const PassArgs<T>& a, const VBlock& vb) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = field_of(a);
+  const int f = field_of(a, vb);
   FieldState* st = a.st ? a.st + f : nullptr;
   const bool act = (st ? (st->active != 0) : true) || a.force;
   if (!act && a.ndots == 0) return;
@@ -822,7 +915,7 @@ __global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
   const int L = a.fft.L, half = L >> 1;
   const bool three_d = a.nz > 1;
   const int nseq = three_d ? a.kxn * a.ny : a.kxn;
-  const int seq0 = blockIdx.x * a.W;
+  const int seq0 = vb.x * a.W;
   const int nvalid = min(a.W, nseq - seq0);
   C* S = reinterpret_cast<C*>(three_d ? a.S2 : a.S1) + (long long)f * a.SP + (long long)seq0 * L;
   Acc<T> acc[3];
@@ -885,23 +978,28 @@ __global__ void GAD_BOUNDS_FILT(T, E) k_filt(PassArgs<T> a) {
     acc[1].s = p1;
     acc[2].s = p2;
   }
-  if (a.ndots) block_finish(a, acc, f, act);
+  if (a.ndots) block_finish(a, acc, f, act, vb);
+}
+
+template <typename T, int E>
+__global__ void GAD_BOUNDS_FILT(T, E) k_filt(const __grid_constant__ PassArgs<T> a) {
+  filt_body<T, E>(a, own_block());
 }
 
 // 3D forward y pass: W consecutive z at one kx; the first stage reads the
 // S1 rows [z][kx][:] directly, the tile is stored transposed into S2
 // [kx][ky][z].  Grid x = kxn * (nz/W).
 template <typename T, int E>
-__global__ void GAD_BOUNDS(T, E) k_yfwd(PassArgs<T> a) {
+__device__ __forceinline__ void yfwd_body(const PassArgs<T>& a, const VBlock& vb) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = field_of(a);
+  const int f = field_of(a, vb);
   if (a.st && !a.st[f].active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int L = a.ny;
   const int zt = a.nz / a.W;
-  const int kx = blockIdx.x / zt, z0 = (blockIdx.x - kx * zt) * a.W;
+  const int kx = vb.x / zt, z0 = (vb.x - kx * zt) * a.W;
   const C* S1 = reinterpret_cast<const C*>(a.S1) + (long long)f * a.SP;
   const int kxn = a.kxn;
   auto load = [&](int w, int i) -> C { return S1[((long long)(z0 + w) * kxn + kx) * L + i]; };
@@ -913,19 +1011,24 @@ __global__ void GAD_BOUNDS(T, E) k_yfwd(PassArgs<T> a) {
   store_transposed(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
 }
 
+template <typename T, int E>
+__global__ void GAD_BOUNDS(T, E) k_yfwd(const __grid_constant__ PassArgs<T> a) {
+  yfwd_body<T, E>(a, own_block());
+}
+
 // 3D inverse y pass: transposed load from S2, inverse FFT whose last stage
 // writes the S1 rows directly.
 template <typename T, int E>
-__global__ void GAD_BOUNDS(T, E) k_yinv(PassArgs<T> a) {
+__device__ __forceinline__ void yinv_body(const PassArgs<T>& a, const VBlock& vb) {
   using C = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* s = reinterpret_cast<C*>(smem_raw);
-  const int f = field_of(a);
+  const int f = field_of(a, vb);
   if (a.st && !a.st[f].active && !a.force) return;
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int L = a.ny;
   const int zt = a.nz / a.W;
-  const int kx = blockIdx.x / zt, z0 = (blockIdx.x - kx * zt) * a.W;
+  const int kx = vb.x / zt, z0 = (vb.x - kx * zt) * a.W;
   const C* S2 = reinterpret_cast<const C*>(a.S2) + (long long)f * a.SP + (long long)kx * L * a.nz + z0;
   load_transposed(s, a.ld, S2, a.nz, a.W, L, tid, nthr);
   C* S1 = reinterpret_cast<C*>(a.S1) + (long long)f * a.SP;
@@ -935,6 +1038,44 @@ __global__ void GAD_BOUNDS(T, E) k_yinv(PassArgs<T> a) {
   if (!fft_run_fixed<C, E, true, 512>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false) &&
       !fft_run_fixed<C, E, true, 256>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false))
     fft_run<C, E, true>(s, a.ld, a.fft, tid, a.tfft, rows, emit, true, false);
+}
+
+template <typename T, int E>
+__global__ void GAD_BOUNDS(T, E) k_yinv(const __grid_constant__ PassArgs<T> a) {
+  yinv_body<T, E>(a, own_block());
+}
+
+// One pass over several shape groups in a single launch: block b belongs to
+// the group g with start[g] <= b < start[g + 1] and runs that group's pass
+// (its PassArgs, copied to shared memory) at its place in the group's own
+// launch shape (vgx x vgy blocks). Blocks of different groups differ in tile
+// shape and FFT plan; the block size and shared memory are the maximum over
+// the groups (threads beyond a group's FFT thread count only join barriers).
+template <typename T, int E, int KIND>
+__global__ void GAD_BOUNDS(T, E) k_multi(const PassArgs<T>* __restrict__ args, const int* __restrict__ start,
+                                         int ngroups) {
+  __shared__ PassArgs<T> sa;
+  __shared__ int sg;
+  if (threadIdx.x == 0) {
+    int g = 0;
+    while (g + 1 < ngroups && (int)blockIdx.x >= start[g + 1]) ++g;
+    sg = g;
+  }
+  __syncthreads();
+  {
+    static_assert(sizeof(PassArgs<T>) % 4 == 0, "PassArgs copies as 32-bit words");
+    const int* src = reinterpret_cast<const int*>(args + sg);
+    int* dst = reinterpret_cast<int*>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(PassArgs<T>) / 4); i += blockDim.x) dst[i] = src[i];
+  }
+  const int local = (int)blockIdx.x - start[sg];
+  __syncthreads();
+  const VBlock vb{local % sa.vgx, local / sa.vgx, sa.vgx, sa.vgy};
+  if constexpr (KIND == 0) xfwd_body<T, E>(sa, vb);
+  else if constexpr (KIND == 1) xinv_body<T, E>(sa, vb);
+  else if constexpr (KIND == 2) filt_body<T, E>(sa, vb);
+  else if constexpr (KIND == 3) yfwd_body<T, E>(sa, vb);
+  else if constexpr (KIND == 4) yinv_body<T, E>(sa, vb);
 }
 
 // u += alpha p for fields whose last CG pass still owes it (Algorithm 3,
