@@ -19,15 +19,15 @@
 // wrap around the ring the MMA is split in two. Every slot starts at zero (the
 // epilogue clears a slot after reading it) and every MMA accumulates.
 // A_{dz, y', dx} is not materialised: the staged rows hold every point of the
-// segment plus one periodic neighbour on each side, 16 bytes (8 channels) per
-// point and channel group, in the no-swizzle K-major core-matrix layout with
-// consecutive points 16 bytes apart, so the x offset of a tap is a shift of
-// the descriptor's start address by 16 bytes. The warps have one role each
+// segment plus one periodic neighbour on each side, one 64-byte row (its 32
+// channels) per point in the K-major layout with the 64-byte swizzle, so the
+// x offset of a tap is a shift of the descriptor's start address by one row
+// and the second half of K a shift by 32 bytes. The warps have one role each
 // and hand work over through mbarriers:
-//   warp 4 (producer): stages input rows (three z planes x four channel
-//     groups: TMA for the 128 interior points, plain loads for the two periodic
-//     neighbours) into a ring of five slots, refilling a slot as soon as the
-//     MMAs of the row it held have completed;
+//   warp 4 (producer): stages input rows (three z planes: one TMA load of the
+//     128 interior points each, swizzled on the way in, and plain loads of the
+//     two periodic neighbours, fetched one row ahead) into a ring of six slots,
+//     refilling a slot as soon as the MMAs of the row it held have completed;
 //   warp 5 (MMA): allocates the tensor memory, and for each input row waits
 //     for its staging (and for the slot of the output row entering the ring to
 //     be cleared), issues its MMAs, and commits them to the "empty" barrier of
@@ -59,11 +59,10 @@ namespace {
 constexpr int kTM = 128;                       // points per tile (GEMM M)
 constexpr int kCh = 32;                        // channels
 constexpr int kTaps = 27;
-constexpr int kPlaneEntries = 144;             // 16-byte entries per channel-group plane
-constexpr int kPlane = kPlaneEntries * 16;     // 2304 bytes
-constexpr int kInterior = 8;                   // entry of the segment's first point (128-byte aligned)
-constexpr int kRow = 4 * kPlane;               // one staged row: 4 channel groups
-constexpr int kSlots = 5;                      // y positions in the ring
+constexpr int kPt = 64;                        // bytes per staged point: its 32 channels, one swizzled row
+constexpr int kInterior = 8;                   // row of the segment's first point (512-byte aligned)
+constexpr int kRow = 144 * kPt;                // one staged z plane: 144 point rows (9216 bytes)
+constexpr int kSlots = 6;                      // y positions in the ring
 constexpr int kBBlock = 96 * 16 * 2;            // B operand of one (dz, dx, K half): 96 x 16 bf16
 constexpr int kWBytes = 9 * 2 * kBBlock;          // all of them (55296 bytes)
 constexpr int kRowsOff = kWBytes;              // staged rows after the weights
@@ -73,13 +72,14 @@ constexpr int kSmemUsed = kBarOff + 512;
 // descriptor can reach under either reading of its two stride fields stays
 // inside the allocation
 constexpr int kSmemAlloc = 227 * 1024;
-constexpr int kTxBytes = 3 * 4 * kTM * 16;     // bytes of one ring fill (3 rows x 4 groups x 128 points)
+constexpr int kTxBytes = 3 * kTM * kPt;       // bytes of one ring fill (3 planes x 128 points x 64 bytes)
 constexpr int kAcc = 16;                       // output-row accumulators in tensor memory
 constexpr uint32_t kTmemCols = 32 * kAcc;      // 32 float32 columns each: all 512 columns
 constexpr int kThreads = 192;                  // 4 epilogue warps, producer warp, MMA warp
 
 static_assert(kSmemUsed <= kSmemAlloc, "shared-memory layout exceeds the allocation");
-static_assert(kPlane % 128 == 0 && kRow % 1024 == 0 && kRowsOff % 1024 == 0, "TMA destinations 128-byte aligned");
+static_assert(kRow % 1024 == 0 && kRowsOff % 1024 == 0 && (kInterior * kPt) % 512 == 0,
+              "TMA destinations aligned to the 512-byte period of the 64-byte swizzle");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -114,6 +114,19 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t 
          ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// Shared-memory matrix descriptor, K-major with the 64-byte swizzle: rows of
+// 64 bytes (32 bf16 of K) whose four 16-byte chunks are permuted by
+// chunk ^= bits 7-8 of the row's shared-memory address (the layout a TMA load
+// with the 64-byte swizzle writes), 8-row groups 512 bytes apart (stride
+// offset), the leading offset unused (encoded as 1), layout type 4. The
+// tensor cores apply the permutation to the final addresses, so a start
+// address shifted by whole 64-byte rows, or by 32 bytes for the second half
+// of K, addresses the shifted matrix.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(512 >> 4) << 32) | (1ull << 46) |
+         (4ull << 61);
+}
+
 // Instruction descriptor of tcgen05.mma kind::f16: D float32, A and B bf16,
 // both K-major, M = 128, N given (a multiple of 16, at most 256).
 __device__ __forceinline__ uint32_t idesc_n(int n) {
@@ -129,12 +142,10 @@ __device__ __forceinline__ void mma_f16(uint32_t dtmem, uint64_t a, uint64_t b, 
       : "memory");
 }
 
-__device__ __forceinline__ void tma_load4(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                          uint32_t bar) {
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, uint32_t bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];"
-      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
       : "memory");
 }
 
@@ -169,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
   const int yc = r / a.Z;
   const int b = blockIdx.y;
   const int x0 = xs * kTM, yb = yc * a.ychunk, ny = a.ychunk;
-  // barriers: full[5] / empty[5] (input ring slot staged / read by its MMAs),
+  // barriers: full[kSlots] / empty[kSlots] (input ring slot staged / read by its MMAs),
   // accf[16] (output row's accumulator complete), acce[16] (read back and cleared)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kBarOff);
   const uint32_t full0 = su32(bars), empty0 = full0 + 8 * kSlots, accf0 = empty0 + 8 * kSlots,
@@ -242,8 +253,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
   // bounded wait that also gives up when another role has aborted
   auto wait = [&](uint32_t bar, uint32_t parity) -> bool {
     if (a.wait_ns == 0) return false;
-    const uint64_t t0 = gtime();
-    for (;;) {
+    {
+      // fast path: a phase that has completed costs no timer read
       uint32_t done;
       asm volatile(
           "{\n\t.reg .pred p;\n\t"
@@ -253,36 +264,70 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
           : "r"(bar), "r"(parity)
           : "memory");
       if (done) return true;
-      if (*abort_flag || gtime() - t0 > a.wait_ns) return false;
     }
+    // the abort flag and the timer are read every 64 polls only: polling
+    // competes with the tensor cores for shared-memory bandwidth
+    const uint64_t t0 = gtime();
+    for (unsigned it = 1;; ++it) {
+      uint32_t done;
+      // suspend hint 20 us: the thread sleeps until the phase completes
+      // instead of polling
+      asm volatile(
+          "{\n\t.reg .pred p;\n\t"
+          "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(bar), "r"(parity), "r"(20000u)
+          : "memory");
+      if (done) return true;
+      if ((it & 63u) == 0u && (*abort_flag || gtime() - t0 > a.wait_ns)) return false;
+    }
+  };
+  // the same wait for a whole warp: lane 0 polls, the others wait for its
+  // answer at the shuffle (ordered after lane 0's observation of the phase)
+  auto wait_warp = [&](uint32_t bar, uint32_t parity) -> bool {
+    bool ok = false;
+    if (lane == 0) ok = wait(bar, parity);
+    return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
   };
 
   if (warp == 4) {
-    // ---- producer: input rows i = 0 .. nrows-1 (y position yb - 1 + i) into slot i % 5
+    // ---- producer: input rows i = 0 .. nrows-1 (y position yb - 1 + i) into
+    // slot i % kSlots: per z plane one TMA load of the 128 interior points
+    // (rows kInterior ..), and the two periodic neighbours (rows kInterior - 1
+    // and kInterior + 128) by lanes 0-23, 16 bytes each (plane lane / 8, side
+    // (lane / 4) & 1, chunk lane & 3), loaded one input row ahead so that
+    // their latency overlaps the previous row's staging
+    const int hzi = lane >> 3, hside = (lane >> 2) & 1, hc = lane & 3;
+    const int hx = hside ? wrapi(x0 + kTM, a.X) : wrapi(x0 - 1, a.X);
+    auto halo_load = [&](int i) -> uint4 {
+      const long long row = (long long)b * plane_rows + (long long)wrapi(z + hzi - 1, a.Z) * a.Y + wrapi(yb - 1 + i, a.Y);
+      return *reinterpret_cast<const uint4*>(a.Hin + (row * a.X + hx) * kCh + hc * 8);
+    };
+    uint4 hv = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < 24) hv = halo_load(0);
     for (int i = 0; i < nrows; ++i) {
       const int s = i % kSlots;
       bool ok = true;
-      if (i >= kSlots) ok = wait(empty0 + 8 * s, (uint32_t)(((i / kSlots) - 1) & 1));
-      ok = __all_sync(0xffffffffu, ok);
+      if (i >= kSlots) ok = wait_warp(empty0 + 8 * s, (uint32_t)(((i / kSlots) - 1) & 1));
       if (!ok) { *abort_flag = 1; break; }
-      const int yw = wrapi(yb - 1 + i, a.Y);
-      if (lane < 24) {       // periodic neighbours (entries 7 and 136) of the 3 rows x 4 channel groups
-        const int zi = lane >> 3, g = (lane >> 1) & 3, side = lane & 1;
-        const long long row = (long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw;
-        const int x = side ? wrapi(x0 + kTM, a.X) : wrapi(x0 - 1, a.X);
-        const uint4 v = *reinterpret_cast<const uint4*>(a.Hin + (row * a.X + x) * kCh + g * 8);
-        *reinterpret_cast<uint4*>(sm + row_smem(s, zi) + g * kPlane + (side ? kInterior + kTM : kInterior - 1) * 16) =
-            v;
+      if (lane < 24) {
+        const uint32_t ra = sbase + row_smem(s, hzi) + (hside ? kInterior + kTM : kInterior - 1) * kPt;
+        const uint32_t dst = ra + ((uint32_t)(hc ^ ((ra >> 7) & 3)) << 4);
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(hv.x), "r"(hv.y), "r"(hv.z), "r"(hv.w)
+                     : "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        if (i + 1 < nrows) hv = halo_load(i + 1);
       }
       __syncwarp();
       if (lane == 0) {
         const uint32_t bar = full0 + 8 * s;
+        const int yw = wrapi(yb - 1 + i, a.Y);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kTxBytes) : "memory");
+#pragma unroll
         for (int zi = 0; zi < 3; ++zi) {
-          const long long row = (long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw;
-          for (int g = 0; g < 4; ++g)
-            tma_load4(sbase + row_smem(s, zi) + g * kPlane + kInterior * 16, &tmap, 0, g, x0, (int)row, bar);
+          const int row = (int)((long long)b * plane_rows + (long long)wrapi(z + zi - 1, a.Z) * a.Y + yw);
+          tma_load3(sbase + row_smem(s, zi) + kInterior * kPt, &tmap, 0, x0, row, bar);
         }
         *rows_issued = i + 1;
       }
@@ -292,6 +337,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
     // ---- MMA issue (lane 0): input row i = y' - (yb - 1) touches output rows
     // m = i, i - 1, i - 2 (relative to yb) through dy = 0, 1, 2
     if (lane == 0) {
+      // descriptors of the first A tile (slot 0, dz = dx = kc = 0) and the
+      // first B block (dz = dx = kc = 0, dy = 0)
+      const uint64_t a0 = sdesc_sw64(sbase + kRowsOff + (kInterior - 1) * kPt);
+      const uint64_t b0 = sdesc(sbase, kBBlock / 2, 128);
       for (int i = 0; i < nrows; ++i) {
         bool ok = wait(full0 + 8 * (i % kSlots), (uint32_t)((i / kSlots) & 1));
         if (ok) *rows_ready = i + 1;
@@ -310,18 +359,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
             const int g0 = i - m0;                                  // tap dy of output row m0
             const uint32_t dt = tmem + (uint32_t)(s0 * 32);
             const uint32_t idesc = idesc_n(32 * run);
-#pragma unroll 1
-            for (int dz = 0; dz < 3; ++dz) {
-              const uint32_t rb = sbase + row_smem(i % kSlots, dz);
-#pragma unroll 1
+            // the 18 MMAs of the run: their descriptors differ from the row's
+            // first ones by compile-time offsets (in 16-byte units of the
+            // start-address field, which stays below 2^14 inside shared
+            // memory), so the issuing thread spends a few instructions per MMA
+            const uint64_t arow = a0 + (uint64_t)((i % kSlots) * (3 * kRow / 16));
+            const uint64_t brow = b0 + (uint64_t)(g0 * (512 / 16));
+#pragma unroll
+            for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
               for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-                for (int kc = 0; kc < 2; ++kc) {
-                  const uint64_t ad = sdesc(rb + 2 * kc * kPlane + (kInterior - 1 + dx) * 16, kPlane, 128);
-                  const uint64_t bd = sdesc(sbase + ((dz * 3 + dx) * 2 + kc) * kBBlock + g0 * 512, kBBlock / 2, 128);
-                  mma_f16(dt, ad, bd, idesc);
-                }
-            }
+                for (int kc = 0; kc < 2; ++kc)
+                  mma_f16(dt, arow + (uint64_t)((dz * kRow + dx * kPt + kc * 32) / 16),
+                          brow + (uint64_t)((((dz * 3 + dx) * 2 + kc) * kBBlock) / 16), idesc);
             m0 -= run;
             cnt -= run;
           }
@@ -346,8 +397,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_conv_tc(const __grid_constant__
     for (int q = 0; q < 32; ++q) zr[q] = 0u;
     for (int m = 0; m < ny; ++m) {
       const int sl = acc_slot(m);
-      bool ok = wait(accf0 + 8 * sl, (uint32_t)((m / kAcc) & 1));
-      ok = __all_sync(0xffffffffu, ok);
+      const bool ok = wait_warp(accf0 + 8 * sl, (uint32_t)((m / kAcc) & 1));
       if (!ok) { *abort_flag = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       uint32_t v[32];
@@ -484,17 +534,19 @@ cudaError_t conv_tc_forward(const __nv_bfloat16* Hin, const __nv_bfloat16* Wimg,
                             const __nv_bfloat16* Hmask, int X, int Y, int Z, int B, int mode, int* flag,
                             unsigned long long wait_ns, cudaStream_t s) {
   if (!conv_tc_shape_ok(X, Y, Z) || B < 1 || ((uintptr_t)Hin & 15)) return cudaErrorInvalidValue;
+  if ((long long)B * Z * Y >= (1LL << 31)) return cudaErrorInvalidValue;     // TMA row coordinates are int32
   EncodeTiledFn enc = encode_fn();
   if (!enc) return cudaErrorNotSupported;
-  // H as a 4D tensor (8 channels, 4 channel groups, X points, B*Z*Y rows) of bf16
+  // H as a 3D tensor (32 channels, X points, B*Z*Y rows) of bf16; a box is
+  // 128 points of one row, written to shared memory with the 64-byte swizzle
   CUtensorMap map;
   std::memset(&map, 0, sizeof map);
-  const cuuint64_t dims[4] = {8, 4, (cuuint64_t)X, (cuuint64_t)B * Z * Y};
-  const cuuint64_t strides[3] = {16, 64, (cuuint64_t)X * 64};
-  const cuuint32_t box[4] = {8, 1, (cuuint32_t)kTM, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<__nv_bfloat16*>(Hin), dims, strides,
-                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+  const cuuint64_t dims[3] = {(cuuint64_t)kCh, (cuuint64_t)X, (cuuint64_t)B * Z * Y};
+  const cuuint64_t strides[2] = {(cuuint64_t)kPt, (cuuint64_t)X * kPt};
+  const cuuint32_t box[3] = {(cuuint32_t)kCh, (cuuint32_t)kTM, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(Hin), dims, strides,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
   int dev = 0, nsm = 152;
