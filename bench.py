@@ -189,6 +189,23 @@ def _traffic(kind, op, space):
     return None
 
 
+def _traffic_conv():
+    """DRAM bytes of one 32 -> 32 layer launch on the 512^3 x 3 velocity from
+    profiles/traffic.json (a 256^3 x 1 ncu capture scaled by the grid points:
+    the layer streams its input and output once), or None when absent or taken
+    with another source of the tensor-core kernel."""
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tp):
+        return None
+    with open(tp) as f:
+        td = json.load(f)
+    with open(os.path.join(ROOT, "paper_1707_09177_gb300", "csrc", "conv_tc.cu"), "rb") as fh:
+        sha = hashlib.sha256(fh.read()).hexdigest()[:16]
+    if td.get("conv_sha") == sha:
+        return td.get("conv_bytes_per_launch_512cubed_x3")
+    return None
+
+
 def _oracle_solve_seconds(ub64, gamma, method, passes):
     """Wall time of one oracle solve with a fixed number of passes (includes
     the initial residual and the final true-residual check)."""
@@ -700,7 +717,7 @@ def _roofline_conv(gad, line):
     ach = flops / (ms * 1e-3) / 1e12
     line["roofline_conv"] = {"bound": "tensor", "kernel": "k_conv_tc" if tc else "k_conv_mma", "achieved": ach,
                              "peak": peak, "unit": "TFLOP/s", "frac": ach / peak, "ms": ms,
-                             "peak_source": src + " bf16_tflops (cuBLAS, burst)", "traffic": None,
+                             "peak_source": src + " bf16_tflops (cuBLAS, burst)", "traffic": _traffic_conv(),
                              "workload": "velocity3d_512_f32 learned guess, one 32->32 layer, 3 components"}
 
 
