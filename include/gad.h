@@ -353,9 +353,13 @@ ad_status ad_histogram(ad_ctx* ctx, ad_dtype dtype, int64_t n, const void* x, do
 ad_status ad_curl(ad_ctx* ctx, const ad_grid* grid, int nvel, const void* u, void* omega, void* stream);
 
 /* Time limit of the bounded device waits (the preconditioner's wait for its
- * staged rows; default 1e9 ns). A block whose wait runs out takes no part in
- * the result, waits up to 1 s more for its own copies still in flight, and
- * its field ends with AD_ERR_TIMEOUT; the context stays usable. ns = 0 makes
+ * staged rows, and the barrier waits of the learned guess's tensor-core
+ * convolution; default 1e9 ns). A preconditioner block whose wait runs out
+ * takes no part in the result, waits up to 1 s more for its own copies still
+ * in flight, and its field ends with AD_ERR_TIMEOUT; a convolution CTA stops
+ * issuing, drains (bounded) its loads and MMAs in flight and frees its tensor
+ * memory, and the ad_guess_* call returns AD_ERR_TIMEOUT. The context stays
+ * usable. ns = 0 makes
  * every such wait give up at once: that is how the timeout path is tested
  * without a fault. Cached solve graphs are dropped. No counterpart in the
  * paper. */

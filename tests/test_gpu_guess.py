@@ -63,6 +63,30 @@ def test_forward_matches_oracle(gad, shape):
         assert _rel(u0[b] - ub[b], ref - ub[b]) < 3e-2, b
 
 
+def test_tensor_core_wait_times_out_cleanly(gad):
+    """The tensor-core convolution's barrier waits are bounded. With the limit
+    at 0 every wait gives up at once (each CTA still drains, bounded, the TMA
+    loads it has in flight and frees its tensor memory): inference reports
+    AD_ERR_TIMEOUT instead of hanging, and the context then infers exactly
+    what it inferred before."""
+    import torch
+    gamma = 0.1
+    ws = cnn.init_weights(channels=32, seed=3, scale_last=1.0)
+    w = torch.from_numpy(_to_lib(ws)).cuda()
+    _, ub = _pairs((8, 8, 128), 1, gamma)
+    t = torch.from_numpy(ub).cuda()
+    ok = gad.guess_infer(w, t, gamma).cpu().numpy()
+    gad.set_wait_limit(0)
+    try:
+        with pytest.raises(gad.GadError) as e:
+            gad.guess_infer(w, t, gamma)
+        assert e.value.status == gad.AD_ERR_TIMEOUT
+    finally:
+        gad.set_wait_limit(1_000_000_000)
+    again = gad.guess_infer(w, t, gamma).cpu().numpy()
+    np.testing.assert_array_equal(again, ok)
+
+
 @pytest.mark.parametrize("shape", [(8, 16, 32), (8, 8, 128)])
 def test_gradients_match_oracle(gad, shape):
     import torch
