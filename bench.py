@@ -465,6 +465,13 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
     }
 
 
+def _workload_config(args, ws):
+    """The config keys that name the workload (the same in both arms)."""
+    return {"workload": WORKLOAD["name"], "grid": "%dx%d" % WORKLOAD["shape"], "batch_per_gpu": args.batch,
+            "gamma": WORKLOAD["gamma"], "tol": WORKLOAD["tol"], "method": args.method, "space": args.space,
+            "parallelism": "replicas" if ws > 1 else "1 gpu"}
+
+
 def run_reference(args):
     """The CPU oracle timed on the host cores: each step is one BiCGSTAB pass
     over one 2048^2 field; the metric extrapolates the per-pass time to the
@@ -493,7 +500,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "method": args.method},
+            "data": "synthetic", "config": _workload_config(args, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -600,12 +607,10 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "grid": "2048x2048", "batch_per_gpu": B, "gamma": gamma,
-                       "tol": tol, "method": args.method, "space": args.space,
-                       "dots": "f64 (compensated f32 products)",
-                       "l2": "inputs %d MiB per vector, > L2 at batch 16; no flush" % (B * P * 4 >> 20),
-                       "loop": "host" if args.host_loop else "graph while node",
-                       "parallelism": "replicas" if ws > 1 else "1 gpu"},
+            "config": dict(_workload_config(args, ws),
+                           dots="f64 (compensated f32 products)",
+                           l2="inputs %d MiB per vector, > L2 at batch 16; no flush" % (B * P * 4 >> 20),
+                           loop="host" if args.host_loop else "graph while node"),
             "iterations": {"min": min(iters), "max": max(iters), "mean": float(np.mean(iters))},
             "converged": ok, "e2e": e2e, "e2e_equals_device": e2e_same, "gpu_launches": int(launches), "clocks": clocks}
     extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
