@@ -42,3 +42,26 @@ def test_traffic_is_reported_only_for_the_measured_kernels(tmp_path, monkeypatch
 
 def test_whole_job_rate_counts_every_rank():
     assert bench.whole_job_mpoints(1, 16, 2048 * 2048, 0.5) * 4 == bench.whole_job_mpoints(4, 16, 2048 * 2048, 0.5)
+
+
+def test_reference_arm_reports_the_same_workload(monkeypatch, capsys):
+    """bench.py --impl reference prints one contract line on the GPU arm's
+    workload config (the oracle's timing is stubbed: 0.3 s fixed + 0.1 s per
+    pass), with the reference arm's own keys."""
+    import argparse
+
+    import numpy as np
+
+    monkeypatch.setattr(bench, "_oracle_solve_seconds", lambda ub, g, m, n: 0.3 + 0.1 * n)
+    monkeypatch.setattr(bench, "_fields", lambda seeds: [np.zeros((8, 8), dtype=np.float32) for _ in seeds])
+    args = argparse.Namespace(gpus=1, steps=2, warmup=1, impl="reference", method="bicgstab", space="physical",
+                              batch=bench.WORKLOAD["batch"])
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["config"] == bench._workload_config(args, 1)
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    n = bench._golden_count("bicgstab", 0) or 160
+    assert abs(line["value"] - 2048 * 2048 / (0.3 + n * 0.1) / 1e6) < 1e-9
