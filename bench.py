@@ -276,6 +276,7 @@ def _velocity_256(gad, out, extras):
     u_true = torch.from_numpy(v).to(torch.device("cuda", torch.cuda.current_device()))
     ub = gad.filter(u_true, 0.1, ndim=3)
     del u_true
+    _tune(gad, (n, n, n), 0.1, 3)
     r, t = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3))
     its = [int(x) for x in r.iterations]
     rs, ts = _timed(lambda: gad.deconvolve(ub, 0.1, method="bicgstab", tol=1e-6, maxit=2000, ndim=3,
@@ -299,6 +300,9 @@ def _velocity_256(gad, out, extras):
 
 
 def _uneven_48(gad, dev, out):
+    # default tile widths here: tuned plans of different block sizes split the
+    # work-list launches into more launch classes (measured slower), and the
+    # graph branches gained nothing from them
     import torch
     from synth import fields
     shapes = fields.uneven_batch(0)
@@ -415,6 +419,7 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
         torch.cuda.synchronize()
         return r, time.perf_counter() - t
 
+    _tune(gad, (n, n, n), gamma, 3)
     gad.deconvolve(ub, gamma, method="bicgstab", tol=1e-6, maxit=2, ndim=3, history=False)     # plans, graph
     gad.guess_infer(w, ub, gamma)
     plain, t_plain = timed(solve)
@@ -463,6 +468,18 @@ def _learned_512(gad, dev, n=512, npairs=2000, n_train=64, epochs=8, batch=8, lr
                   "seconds": t_train, "loss_per_epoch": [float(x) for x in hist],
                   "data_generation_s": t_gen, "init": "explicit-inverse stencil"},
     }
+
+
+_TUNE = [True]
+
+
+def _tune(gad, shape, gamma, batch, method="bicgstab"):
+    """Tile widths of the plan for (shape, batch) picked by the library's
+    autotuner (every admissible width of every pass timed with CUDA events,
+    the fastest kept), for both iteration spaces; no-op with --no-tune."""
+    if _TUNE[0]:
+        for space in ("physical", "spectral"):
+            gad.autotune(shape, gamma, batch, method=method, space=space)
 
 
 def _workload_config(args, ws):
@@ -521,6 +538,9 @@ def main():
     ap.add_argument("--space", default="physical", choices=["physical", "spectral"],
                     help="iteration space of the timed solve: physical (G by FFT passes every iteration, the "
                          "paper's formulation) or spectral (iterate on the half spectra, G pointwise)")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default tile widths instead of the library's autotuner (ad_autotune) on every "
+                         "plan the benchmark times")
     ap.add_argument("--extras", default="methods,3d512,3d256,closure,uneven48,learned512",
                     help="comma list of extra measurements on rank 0: methods, 3d512 (pass rooflines of the "
                          "512^3 x 3 velocity), 3d256, closure (needs 3d256), uneven48, learned512")
@@ -545,6 +565,8 @@ def main():
     gad.load()
     if args.host_loop:
         gad.set_graph_mode(False)
+    _TUNE[0] = not args.no_tune
+    _tune(gad, n, gamma, B, args.method)
 
     # inputs: true fields from the seeded generator, filtered by the library
     u_true = torch.from_numpy(_fields(seeds)).to(dev)
@@ -610,7 +632,8 @@ def main():
             "config": dict(_workload_config(args, ws),
                            dots="f64 (compensated f32 products)",
                            l2="inputs %d MiB per vector, > L2 at batch 16; no flush" % (B * P * 4 >> 20),
-                           loop="host" if args.host_loop else "graph while node"),
+                           loop="host" if args.host_loop else "graph while node",
+                           tiles="autotuned (ad_autotune)" if _TUNE[0] else "default"),
             "iterations": {"min": min(iters), "max": max(iters), "mean": float(np.mean(iters))},
             "converged": ok, "e2e": e2e, "e2e_equals_device": e2e_same, "gpu_launches": int(launches), "clocks": clocks}
     extras = set() if args.no_extras else set(x for x in args.extras.split(",") if x)
@@ -703,6 +726,7 @@ def _roofline_3d512(gad, line, method="bicgstab"):
     P = n[0] * n[1] * n[2]
     SP = (n[2] // 2 + 1) * n[0] * n[1]
     peak, src = _peaks()
+    _tune(gad, n, gamma, B, method)
     passes = _pass_table(gad, n, gamma, B, method, "physical", P, SP, reps=5)
     ent = _roofline_entry(passes, peak, src, "physical3d")
     ent["solve"] = _solve_entry(gad, passes, n, gamma, B, method, "physical", peak, src, reps=5)
