@@ -312,3 +312,10 @@ def test_bench_workload_full_size(gad):
     res = gad.deconvolve(t, 0.01, method="bicgstab", tol=0.0, maxit=3, ndim=2)
     ref = oracle.bicgstab(ub[5].astype(np.float64), 0.01, tol=0.0, maxit=3, precision="f32")
     assert _rel(res.u[5].double().cpu().numpy(), ref.u) < 1e-5
+    # the launch shapes the benchmark times: tile widths picked by the autotuner
+    gad.autotune((n, n), 0.01, batch, method="bicgstab")
+    res = gad.deconvolve(t, 0.01, method="bicgstab", tol=1e-6, maxit=3000, true_residual=True, ndim=2)
+    assert np.all(res.status == gad.AD_OK), res.status
+    assert np.all(res.true_residual < 50e-6)
+    res = gad.deconvolve(t, 0.01, method="bicgstab", tol=0.0, maxit=3, ndim=2)
+    assert _rel(res.u[5].double().cpu().numpy(), ref.u) < 1e-5
