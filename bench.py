@@ -19,6 +19,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import subprocess
 import sys
 import tempfile
@@ -518,7 +519,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(ts)) * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _workload_config(args, ws),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "cpu_model": _host_cpu()[0], "host_cores": _host_cpu()[1]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -696,9 +698,17 @@ def _solve_entry(gad, passes, shape, gamma, B, method, space, peak, src, reps=10
     body_ms = gad.time_body(shape, gamma, B, method=method, reps=reps, space=space)
     nbytes = float(sum(p["bytes"] for p in passes))
     ach = nbytes / (body_ms * 1e-3) / 1e9
-    return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_source": src + " hbm_gbs (copy, burst)", "bytes_per_body": nbytes, "ms_per_body": body_ms,
-            "launches_per_body": len(passes), "sum_of_pass_ms": float(sum(p["ms"] for p in passes))}
+    ent = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+           "peak_source": src + " hbm_gbs (copy, burst)", "bytes_per_body": nbytes, "ms_per_body": body_ms,
+           "launches_per_body": len(passes), "sum_of_pass_ms": float(sum(p["ms"] for p in passes))}
+    # the same body by DRAM bytes (ncu, profiles/traffic.json) when every pass has a capture
+    key = space + ("3d" if len(shape) == 3 else "")
+    tr = [_traffic(p["kind"], p["op"], key) for p in passes]
+    if tr and all(t is not None for t in tr):
+        dram = float(sum(tr)) / (body_ms * 1e-3) / 1e9
+        ent["dram"] = {"bytes_per_body": float(sum(tr)), "achieved": dram, "frac": dram / peak,
+                       "source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch"}
+    return ent
 
 
 def _rooflines(gad, line, args, n, gamma, B):
@@ -758,6 +768,22 @@ def _bf16_peak():
     return 1900.0, "fallback"
 
 
+def _host_cpu():
+    """The host's CPU model (from /proc/cpuinfo where present) and logical cores."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                key = ln.split(":")[0].strip().lower()
+                if key in ("model name", "cpu part", "hardware"):
+                    model = ln.split(":", 1)[1].strip()
+                    if key == "model name":
+                        break
+    except OSError:
+        pass
+    return model, os.cpu_count()
+
+
 def _cpu_baseline(line, ubar_host, gamma, method, n0, P):
     """The oracle on this host's cores (one thread), bounded sample: a 0-pass
     and a 4-pass solve of field 0, extrapolated to the GPU's pass count."""
@@ -766,7 +792,9 @@ def _cpu_baseline(line, ubar_host, gamma, method, n0, P):
     sample_passes = 4
     t_solve, per, t0 = _oracle_estimate(ub0, gamma, method, n0, sample_passes)
     cpu_val = P / t_solve / 1e6
+    model, ncpu = _host_cpu()
     line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "cpu_model": model, "host_cores": ncpu,
                             "sample": ("oracle %s (float64 NumPy, 1 thread), field 0 of the batch: a 0-pass "
                                        "solve (%.2f s fixed cost) and a %d-pass solve (%.2f s per pass), "
                                        "extrapolated to the %d passes the GPU solve of that field needed"

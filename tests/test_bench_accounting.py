@@ -65,3 +65,21 @@ def test_reference_arm_reports_the_same_workload(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     n = bench._golden_count("bicgstab", 0) or 160
     assert abs(line["value"] - 2048 * 2048 / (0.3 + n * 0.1) / 1e6) < 1e-9
+
+
+def test_body_dram_fraction_uses_the_captured_bytes(monkeypatch):
+    """roofline_solve reports the body's DRAM-byte rate (ncu bytes per launch
+    from profiles/traffic.json) beside its algorithmic rate, only when every
+    pass of the body has a capture."""
+    class FakeLib:
+        @staticmethod
+        def time_body(shape, gamma, B, method, reps, space):
+            return 2.0                                      # ms
+    passes = [{"kind": "xfwd", "op": 3, "bytes": 4e9, "ms": 1.0}, {"kind": "filt", "op": 0, "bytes": 2e9, "ms": 1.0}]
+    captured = {("xfwd", 3, "physical"): 3e9, ("filt", 0, "physical"): 1e9}
+    monkeypatch.setattr(bench, "_traffic", lambda k, o, sp: captured.get((k, o, sp)))
+    ent = bench._solve_entry(FakeLib, passes, (64, 64), 0.1, 1, "bicgstab", "physical", 1000.0, "measured")
+    assert abs(ent["achieved"] - 3000.0) < 1e-9 and abs(ent["frac"] - 3.0) < 1e-12
+    assert abs(ent["dram"]["bytes_per_body"] - 4e9) < 1e-3 and abs(ent["dram"]["frac"] - 2.0) < 1e-12
+    captured.pop(("filt", 0, "physical"))
+    assert "dram" not in bench._solve_entry(FakeLib, passes, (64, 64), 0.1, 1, "bicgstab", "physical", 1000.0, "m")
