@@ -779,6 +779,11 @@ def _host_cpu():
                     model = ln.split(":", 1)[1].strip()
                     if key == "model name":
                         break
+                    if key == "cpu part":
+                        # Arm part numbers of /proc/cpuinfo
+                        model = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1",
+                                 "0xd0c": "Arm Neoverse N1", "0xd49": "Arm Neoverse N2"}.get(model.lower(),
+                                                                                           "Arm cpu part " + model)
     except OSError:
         pass
     return model, os.cpu_count()
