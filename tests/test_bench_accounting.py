@@ -83,3 +83,19 @@ def test_body_dram_fraction_uses_the_captured_bytes(monkeypatch):
     assert abs(ent["dram"]["bytes_per_body"] - 4e9) < 1e-3 and abs(ent["dram"]["frac"] - 2.0) < 1e-12
     captured.pop(("filt", 0, "physical"))
     assert "dram" not in bench._solve_entry(FakeLib, passes, (64, 64), 0.1, 1, "bicgstab", "physical", 1000.0, "m")
+
+
+def test_3d_bicgstab_pass_bytes():
+    """A 3D BiCGSTAB pass adds the y passes around each filter pass: per G the
+    spectrum goes S1 -> S2 (forward y), S2 -> S2 (filter along z), S2 -> S1
+    (inverse y); 15 field vectors and 16 spectra per pass (the 31
+    vector-equivalents of the design notes, of which a fused yz-plane pass
+    would remove 8 spectra)."""
+    n, B = 512, 3
+    P, SP = n ** 3, (n // 2 + 1) * n * n
+    v, s = 4 * P * B, 8 * SP * B
+    body = [("xfwd", 3), ("yfwd", 3), ("filt", 0), ("yinv", 0), ("xinv", 6),
+            ("xfwd", 4), ("yfwd", 4), ("filt", 2), ("yinv", 2), ("xinv", 7)]
+    got = [bench._pass_bytes(k, o, P, SP, B, "bicgstab") for k, o in body]
+    assert sum(got) == 15 * v + 16 * s
+    assert got[1] == got[2] == got[3] == 2 * s
